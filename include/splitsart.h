@@ -1,0 +1,297 @@
+/*
+ * splitsart.h: C ABI of the GB300 (sm_103a) symmetric-split SART library.
+ *
+ * The library follows Alikhanov et al., "About one method of parallelization
+ * of calculations during the reconstruction of a tomographic image"
+ * (arXiv:1902.10559):
+ * - A slice's system A f = p (Eq. 1) whose matrix satisfies
+ *   w_{i,j} = w_{M-i+1,N-j+1} (Eq. 2) is folded into two independent systems,
+ *   A1 f1 = p1 and A2 f2 = p2 (Eqs. 3, 4). Each has M/2 rows and N/2 columns.
+ * - Each system is solved by SART-type iteration.
+ * - The image is recombined by Theorem 1 (Eq. 5).
+ *
+ * Conventions:
+ * - Indices are 0-based. The paper's i <-> M-i+1 is i <-> M-1-i here, and
+ *   j <-> N-j+1 is j <-> N-1-j. Mh = M/2, Nh = N/2.
+ * - Every function returns an int status: 0 on success, a negative
+ *   SPLITSART_ERR_* code on failure. splitsart_last_error() gives the
+ *   message of the calling thread's last failure.
+ * - Handles are opaque and owned by the library. Each is released by its
+ *   *_destroy function. Destroying NULL is a no-op.
+ * - Arguments ending in _dev are device pointers owned by the caller.
+ *   Arguments ending in _host are host pointers owned by the caller. The
+ *   library keeps no pointer to caller memory after a call returns.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream). Device work is enqueued on it, and the call returns without
+ *   synchronising. Functions named *_result, *_export and *_info synchronise
+ *   the system's last stream, because they read device results to the host.
+ * - Vector element type ("vec"): double for SPLITSART_F64 systems, float for
+ *   all others. The pair layout interleaves the two split systems: element
+ *   i of a pair vector is (x1_i, x2_i). Pair vectors are therefore double2 or
+ *   float2 arrays.
+ */
+#ifndef SPLITSART_H
+#define SPLITSART_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SPLITSART_OK 0
+#define SPLITSART_ERR_ARG (-1)        /* bad argument: NULL, size or range */
+#define SPLITSART_ERR_ODD_DIM (-2)    /* nx odd or M odd: the split needs N and M even (Section 2) */
+#define SPLITSART_ERR_ASYMMETRIC (-3) /* the matrix cannot satisfy Eq. (2) */
+#define SPLITSART_ERR_CUDA (-4)       /* a CUDA runtime call failed */
+#define SPLITSART_ERR_TIMEOUT (-5)    /* a bounded device-side wait ran out */
+#define SPLITSART_ERR_NOMEM (-6)      /* device or host allocation failed */
+#define SPLITSART_ERR_STATE (-7)      /* call made in the wrong order */
+#define SPLITSART_ERR_NONFINITE (-8)  /* the input holds NaN or Inf */
+
+/* ---- value storage of the folded matrices ---- */
+#define SPLITSART_F64 0  /* double pairs, double vectors and normalisers */
+#define SPLITSART_F32 1  /* float pairs, float vectors and normalisers */
+#define SPLITSART_BF16 2 /* bf16 codes + per-row float scales; float vectors; double normalisers */
+#define SPLITSART_F16 3  /* fp16 codes + per-row float scales; float vectors; double normalisers */
+
+/* ---- image layouts ---- */
+#define SPLITSART_LAYOUT_SNAKE 0 /* f[N] in vertical-snake order (Section 2, Fig. 1) */
+#define SPLITSART_LAYOUT_IMAGE 1 /* f[nz][nx], row r from the bottom, column c from the left */
+
+/*
+ * Acquisition of one 2D slice (Section 2). Lengths are in mm, angles in
+ * degrees.
+ * - Object: x in [-W/2, W/2], z in [z0, z0+H], with nx x nz cells.
+ * - Sources: K point sources at theta_k = gamma (2k+1-K)/(K-1), at
+ *   (R sin theta_k, R cos theta_k). Source K-1-k is the exact mirror (-x, z)
+ *   of source k (positions pairwise symmetric about OZ).
+ * - Detector: nb bins on z = 0, centred at u_b = D (2b+1-nb)/(2nb).
+ * - Rays: ray i = k nb + b runs from source k to the centre of bin b, so
+ *   M = K nb. Ray M-1-i is the mirror of ray i.
+ * - Voxels: cell (c, r) has vertical-snake index
+ *   j = c nz + (c even ? r : nz-1-r). When nx is even, j <-> N-1-j is the
+ *   mirror about OZ, which gives Eq. (2).
+ */
+typedef struct splitsart_geometry_params {
+    int32_t nx, nz;
+    double W, H, z0;
+    int32_t K;
+    double gamma_deg, R;
+    int32_t nb;
+    double D;
+} splitsart_geometry_params;
+
+typedef struct splitsart_geometry splitsart_geometry; /* host: first M/2 rows of A */
+typedef struct splitsart_system splitsart_system;     /* device: folded A1/A2, CSR + CSC + normalisers */
+
+/*
+ * Build the first Mh rows of A on the host, in FP64.
+ * - Weights: w_ij is the exact (Siddon) length of ray i inside cell j, in mm.
+ * - A ray lying exactly on a vertical cell boundary gives half its length to
+ *   each of the two adjacent cells.
+ * - Rows i >= Mh are never built. Eq. (2) makes them redundant:
+ *   w_{M-1-i, N-1-j} = w_{i,j}.
+ * Errors: SPLITSART_ERR_ODD_DIM if nx is odd or K nb is odd;
+ * SPLITSART_ERR_ARG for non-positive sizes or K < 2.
+ */
+int splitsart_make_geometry(const splitsart_geometry_params* params, splitsart_geometry** out);
+
+/*
+ * Wrap caller-supplied first-half rows of any matrix that satisfies Eq. (2).
+ * For example, the 4 x 6 system of Example 1.
+ * - row_ptr_host[Mh+1] (int64) and col_host/val_host[nnz] hold rows
+ *   0..Mh-1 of A in CSR form, with Mh = M/2. Columns are in [0, N) and
+ *   strictly increasing within a row.
+ * - The data are copied.
+ * Errors: SPLITSART_ERR_ODD_DIM if M or N is odd; SPLITSART_ERR_ARG if the
+ * CSR is malformed; SPLITSART_ERR_NONFINITE for NaN or Inf values.
+ */
+int splitsart_make_geometry_from_csr(int64_t M, int64_t N, const int64_t* row_ptr_host,
+                                     const int32_t* col_host, const double* val_host,
+                                     splitsart_geometry** out);
+
+/* Report M, N and the stored nonzeros of rows 0..Mh-1. Any output may be NULL. */
+int splitsart_geometry_info(const splitsart_geometry* g, int64_t* M, int64_t* N, int64_t* nnz_half);
+
+/* Copy the first-half CSR to host buffers sized from splitsart_geometry_info. */
+int splitsart_geometry_export(const splitsart_geometry* g, int64_t* row_ptr_host, int32_t* col_host,
+                              double* val_host);
+
+void splitsart_geometry_destroy(splitsart_geometry* g);
+
+/*
+ * Fold A into A1 and A2 on the device. The formulas are those after Eq. (4):
+ *     w1_ij = w_ij - w_{M-1-i,j},   w2_ij = w_ij + w_{M-1-i,j},   i < Mh, j < Nh.
+ * Eq. (2) turns the mirror row into a reflection of row i itself:
+ * w_{M-1-i,j} = w_{i,N-1-j}. So each folded row i is a merge of row i's left
+ * half with its reflected right half. Row M-1-i is never read.
+ *
+ * The call:
+ * - allocates the system, sized from an upper bound;
+ * - uploads the half rows;
+ * - runs on `stream`: the fold, a deterministic CSC transpose, and the
+ *   absolute row/column sums with 1/0 := 0.
+ *
+ * A1 and A2 share one column-index pattern. It is the union pattern, and it
+ * keeps exact zeros made by cancellation. `dtype` selects the value storage
+ * (SPLITSART_F64/F32/BF16/F16).
+ * - BF16/F16 store codes q_ij = round(a_ij / s_i), with s_i = max_j |a_ij|
+ *   per row and per system, as an FP32 scale. The division and the rounding
+ *   are done in FP32, round to nearest even.
+ * - The normalisers of a BF16/F16 system are taken, in FP64, from the
+ *   dequantised values s_i q_ij.
+ * Errors: SPLITSART_ERR_ARG, SPLITSART_ERR_NOMEM, SPLITSART_ERR_CUDA.
+ */
+int splitsart_fold_system(const splitsart_geometry* g, int dtype, void* stream, splitsart_system** out);
+
+/*
+ * Re-run the device fold of an existing system from its uploaded half rows.
+ * The fold covers the CSR, the CSC and the normalisers. Nothing is allocated.
+ */
+int splitsart_refold(splitsart_system* sys, void* stream);
+
+typedef struct splitsart_system_info {
+    int64_t M, N, Mh, Nh;
+    int64_t nnz_half;    /* stored entries of rows 0..Mh-1 of A */
+    int64_t S;           /* stored entries of the shared folded pattern */
+    int64_t empty_rows;  /* folded rows with no entry */
+    int64_t exact_zeros; /* entries with w1 = 0 made by cancellation */
+    int32_t dtype;
+    int32_t nx, nz;      /* 0 when the geometry came from a CSR */
+    int64_t device_bytes;
+} splitsart_system_info;
+
+/* Fill *info. This synchronises with the system's last stream, once, to read S. */
+int splitsart_system_info_get(splitsart_system* sys, splitsart_system_info* info);
+
+/*
+ * Copy the folded CSR to the host. Buffer sizes:
+ * - row_ptr_host: Mh+1 entries (int64);
+ * - col_host: S entries (int32);
+ * - a1_host, a2_host: S entries (double). These hold the values the
+ *   iteration uses: for BF16/F16 systems, the dequantised s_i q_ij.
+ * - normalisers (optional, may be NULL): R_host[2 Mh] and C_host[2 Nh],
+ *   interleaved (system 1, system 2). They hold the absolute sums, not their
+ *   reciprocals.
+ * This function is for verification.
+ */
+int splitsart_system_export(splitsart_system* sys, int64_t* row_ptr_host, int32_t* col_host,
+                            double* a1_host, double* a2_host, double* R_host, double* C_host);
+
+/*
+ * Copy the folded CSC (the transpose used by the back-projection) to the host.
+ * Buffer sizes:
+ * - col_ptr_host: Nh+1 entries;
+ * - row_host: S entries;
+ * - a1_host, a2_host: S entries.
+ * Rows within a column are in increasing order.
+ */
+int splitsart_system_export_csc(splitsart_system* sys, int64_t* col_ptr_host, int32_t* row_host,
+                                double* a1_host, double* a2_host);
+
+void splitsart_system_destroy(splitsart_system* sys);
+
+/*
+ * Fold a projection vector as after Eq. (4):
+ *     p1_i = p_i - p_{M-1-i},   p2_i = p_i + p_{M-1-i},   i < Mh.
+ * p_dev: vec[M]. p12_dev: pair[Mh] output.
+ */
+int splitsart_fold_rhs(const splitsart_system* sys, const void* p_dev, void* p12_dev, void* stream);
+
+/*
+ * Fold an image, using the vectors of the proof of Theorem 1:
+ *     f1_j = f_j - f_{N-1-j},   f2_j = f_j + f_{N-1-j},   j < Nh.
+ * This gives a warm start for splitsart_solve.
+ * f_dev: vec[N] in `layout` (SPLITSART_LAYOUT_IMAGE needs a geometry with nx, nz).
+ * f12_dev: pair[Nh] output.
+ */
+int splitsart_fold_image(const splitsart_system* sys, const void* f_dev, int layout, void* f12_dev,
+                         void* stream);
+
+/*
+ * Recombine by Theorem 1, Eq. (5):
+ *     f_j = (f2_j + f1_j)/2,   f_{N-1-j} = (f2_j - f1_j)/2.
+ * f12_dev: pair[Nh]. f_dev: vec[N] output, written in `layout`.
+ */
+int splitsart_recombine(const splitsart_system* sys, const void* f12_dev, void* f_dev, int layout,
+                        void* stream);
+
+/*
+ * Forward projection p = A f of a full image, through the folded system.
+ * Steps: fold f (proof of Theorem 1), apply A1 and A2, then unfold the rays:
+ *     p_i = (q2_i + q1_i)/2,   p_{M-1-i} = (q2_i - q1_i)/2.
+ * This is exact, because A1 f1 = fold1(A f) and A2 f2 = fold2(A f).
+ * f_dev: vec[N] in `layout`. p_dev: vec[M] output.
+ * Arithmetic is in the system's precision.
+ */
+int splitsart_project(splitsart_system* sys, const void* f_dev, int layout, void* p_dev, void* stream);
+
+/*
+ * Options of splitsart_solve. Zero-initialise the struct, then set fields.
+ */
+typedef struct splitsart_solve_opts {
+    int32_t max_iters;     /* iteration cap, >= 0 */
+    double lambda;         /* relaxation, 0 < lambda < 2 */
+    double tol;            /* stop at the first k with rho_k <= tol; 0 = run max_iters */
+    int32_t check_every;   /* test rho every this many iterations (>= 1; 0 means 1) */
+    int32_t block_threads; /* threads per CTA, 0 = library default (256) */
+    int32_t ctas_per_sm;   /* 0 = as many as fit */
+    int32_t lanes_per_col; /* back-projection lanes per column, 0 = default (8); 1,2,4,8,16,32 */
+    int32_t reserved0;
+    double timeout_ms;     /* limit of each grid-barrier wait; 0 = default (2000 ms) */
+    int32_t inject_barrier_fault; /* test hook: the barrier also waits for a CTA that never comes */
+    int32_t reserved1;
+} splitsart_solve_opts;
+
+/*
+ * Solve both split systems by the simultaneous SART-type iteration, in one
+ * persistent cooperative launch. For system s in {1, 2}:
+ *     r^k = p^s - A_s f^k,   u^k_i = r^k_i / R_i,   f^{k+1}_j = f^k_j + lambda (A_s^T u^k)_j / C_j
+ * R and C are the absolute row and column sums, with 1/0 := 0.
+ * The two systems share each pass over the index pattern.
+ *
+ * Stopping: with
+ *     rho_k = sqrt(||r1^k||^2 + ||r2^k||^2) / sqrt(||p1||^2 + ||p2||^2),
+ * which equals ||A f^k - p|| / ||p|| for the recombined image, the solve
+ * returns f^k at the first tested k with rho_k <= tol, or at
+ * k = max_iters. The update is skipped on the stopping pass. The norms are
+ * accumulated in FP64 in a fixed order, so results are bitwise reproducible.
+ *
+ * Arguments:
+ * - p12_dev: pair[Mh] from splitsart_fold_rhs.
+ * - f12_dev: pair[Nh], in = f^0, out = f^k.
+ *
+ * The result (iterations, rho, status) stays on the device until
+ * splitsart_solve_result reads it. Errors found before the launch are
+ * returned directly. A barrier timeout is reported by splitsart_solve_result.
+ */
+int splitsart_solve(splitsart_system* sys, const void* p12_dev, void* f12_dev, const splitsart_solve_opts* opts,
+                    void* stream);
+
+typedef struct splitsart_solve_info {
+    int32_t iters;   /* k of the returned iterate */
+    int32_t status;  /* SPLITSART_OK or SPLITSART_ERR_TIMEOUT */
+    double rho;      /* rho_k of the returned iterate */
+    double rr;       /* ||r1||^2 + ||r2||^2 */
+    double pp;       /* ||p1||^2 + ||p2||^2 */
+} splitsart_solve_info;
+
+/*
+ * Synchronise the system's last stream and read the last solve's result.
+ * Returns info->status, or SPLITSART_ERR_CUDA if the device reports an error.
+ */
+int splitsart_solve_result(splitsart_system* sys, splitsart_solve_info* info);
+
+/* Copy the thread's last error message into buf (truncated, NUL-terminated). Returns its full length. */
+int splitsart_last_error(char* buf, size_t len);
+
+/* Library version string. */
+const char* splitsart_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPLITSART_H */

@@ -1,0 +1,167 @@
+// Device-side building blocks shared by the library's kernels:
+// - value traits for the four storages of the folded matrices;
+// - cache-control loads and stores;
+// - the bounded grid barrier.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/splitsart.h"
+
+namespace splitsart {
+
+// ---------------------------------------------------------------------------
+// Value traits. The two split systems always travel together: matrix values
+// and vectors are stored as interleaved pairs (x1, x2). One pass over the
+// shared index pattern then serves A1 and A2 at once.
+// ---------------------------------------------------------------------------
+struct TF64 {
+    using Pair = double2;  // (a1, a2)
+    using Acc = double;
+    using Vec2 = double2;  // (x1, x2) vectors: f, p, u
+    using Norm2 = double2; // 1/R, 1/C
+    static constexpr bool kQuant = false;
+    static constexpr int kDtype = SPLITSART_F64;
+    __device__ static inline void decode(Pair v, Acc& a1, Acc& a2) { a1 = v.x; a2 = v.y; }
+};
+struct TF32 {
+    using Pair = float2;
+    using Acc = float;
+    using Vec2 = float2;
+    using Norm2 = float2;
+    static constexpr bool kQuant = false;
+    static constexpr int kDtype = SPLITSART_F32;
+    __device__ static inline void decode(Pair v, Acc& a1, Acc& a2) { a1 = v.x; a2 = v.y; }
+};
+struct TBF16 {
+    using Pair = __nv_bfloat162;
+    using Acc = float;
+    using Vec2 = float2;
+    using Norm2 = double2;
+    static constexpr bool kQuant = true;
+    static constexpr int kDtype = SPLITSART_BF16;
+    __device__ static inline void decode(Pair v, Acc& a1, Acc& a2) {
+        float2 f = __bfloat1622float2(v);
+        a1 = f.x;
+        a2 = f.y;
+    }
+    __device__ static inline Pair encode(float q1, float q2) {
+        return __halves2bfloat162(__float2bfloat16_rn(q1), __float2bfloat16_rn(q2));
+    }
+};
+struct TF16 {
+    using Pair = __half2;
+    using Acc = float;
+    using Vec2 = float2;
+    using Norm2 = double2;
+    static constexpr bool kQuant = true;
+    static constexpr int kDtype = SPLITSART_F16;
+    __device__ static inline void decode(Pair v, Acc& a1, Acc& a2) {
+        float2 f = __half22float2(v);
+        a1 = f.x;
+        a2 = f.y;
+    }
+    __device__ static inline Pair encode(float q1, float q2) {
+        return __halves2half2(__float2half_rn(q1), __float2half_rn(q2));
+    }
+};
+
+// Read-only (non-coherent path) loads, for data that no kernel writes
+// during the launch.
+template <class T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ __nv_bfloat162 ldg(const __nv_bfloat162* p) {
+    unsigned v = __ldg(reinterpret_cast<const unsigned*>(p));
+    return *reinterpret_cast<__nv_bfloat162*>(&v);
+}
+template <>
+__device__ __forceinline__ __half2 ldg(const __half2* p) {
+    unsigned v = __ldg(reinterpret_cast<const unsigned*>(p));
+    return *reinterpret_cast<__half2*>(&v);
+}
+
+// L2-coherent loads and stores (bypassing L1), for vectors that other CTAs of
+// the same persistent launch rewrite between grid barriers.
+__device__ __forceinline__ float2 ldcg(const float2* p) { return __ldcg(p); }
+__device__ __forceinline__ double2 ldcg(const double2* p) { return __ldcg(p); }
+__device__ __forceinline__ void stcg(float2* p, float2 v) { __stcg(p, v); }
+__device__ __forceinline__ void stcg(double2* p, double2 v) { __stcg(p, v); }
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v, unsigned width = 32) {
+    for (unsigned o = width >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, width);
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+
+// Control block of one persistent launch. The host zeroes it before each launch.
+struct LaunchCtl {
+    unsigned bar_count;
+    unsigned bar_gen;
+    int err;       // 0, or a SPLITSART_ERR_* code
+    int err_where; // barrier index at which a wait ran out
+};
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).
+// - Thread 0 of each CTA arrives on a counter. The last arriver resets the
+//   counter and advances the generation.
+// - The other CTAs spin on the generation with a wall-clock limit and a spin
+//   cap. If either runs out, the wait records SPLITSART_ERR_TIMEOUT in
+//   ctl->err and stops waiting.
+// - `expected` is normally gridDim.x. A test passes gridDim.x + 1 to make the
+//   wait run out on purpose.
+// Returns false, for every thread of the CTA, if any CTA has recorded an
+// error. The caller must then return.
+__device__ __forceinline__ bool grid_barrier(LaunchCtl* ctl, unsigned expected, unsigned long long timeout_ns,
+                                             int where) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned gen = ld_acquire_gpu(&ctl->bar_gen);
+        __threadfence();
+        const unsigned prev = atomicAdd(&ctl->bar_count, 1u);
+        if (prev == expected - 1) {
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            const unsigned long long max_spins = timeout_ns / 32ull + (1ull << 20);
+            unsigned long long spins = 0;
+            while (ld_acquire_gpu(&ctl->bar_gen) == gen) {
+                if (ld_volatile(&ctl->err) != 0) { ok = 0; break; }
+                if (global_ns() - t0 > timeout_ns || ++spins > max_spins) {
+                    if (atomicCAS(&ctl->err, 0, SPLITSART_ERR_TIMEOUT) == 0) ctl->err_where = where;
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        if (ld_volatile(&ctl->err) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+}  // namespace splitsart

@@ -1,0 +1,482 @@
+// Fold of the system and the small vector kernels around the solve.
+//
+// - Fold of A (formulas after Eq. 4): w1_ij = w_ij - w_{M-1-i,j},
+//   w2_ij = w_ij + w_{M-1-i,j}, i < Mh, j < Nh. Eq. (2) gives
+//   w_{M-1-i,j} = w_{i,N-1-j}, so folded row i needs row i of A alone.
+//   Row i's columns are sorted. Its entries with j < Nh, read forward, and its
+//   entries with j >= Nh, read backward and reflected to N-1-j, are then two
+//   ascending lists. The folded row is their merge. Columns present in both
+//   lists give one entry, (w_d - w_r, w_d + w_r).
+// - Fold of p (after Eq. 4), fold of an image (proof of Theorem 1),
+//   recombination (Theorem 1, Eq. 5), and forward projection through the
+//   folded system.
+// - A deterministic CSC transpose. Columns are counted, scanned and placed
+//   with atomics, then each column is sorted by row. The absolute row and
+//   column sums come last, in FP64, with 1/0 := 0.
+#include <climits>
+#include <cstdio>
+
+#include "device_common.cuh"
+#include "system.h"
+
+namespace splitsart {
+
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Visit folded row i in ascending column order. Call fn(col, w_direct, w_reflected),
+// with 0.0 for an absent side.
+template <class F>
+__device__ __forceinline__ void for_each_folded(const int32_t* __restrict__ hcol, const double* __restrict__ hval,
+                                                int64_t e0, int64_t e1, int N, F&& fn) {
+    const int Nh = N >> 1;
+    int64_t lo = e0, hi = e1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (hcol[mid] < Nh) lo = mid + 1;
+        else hi = mid;
+    }
+    const int64_t m = lo;
+    int64_t a = e0, b = e1 - 1;
+    while (a < m || b >= m) {
+        const int ca = a < m ? hcol[a] : INT_MAX;
+        const int cb = b >= m ? (N - 1 - hcol[b]) : INT_MAX;
+        if (ca < cb) {
+            fn(ca, hval[a], 0.0);
+            ++a;
+        } else if (cb < ca) {
+            fn(cb, 0.0, hval[b]);
+            --b;
+        } else {
+            fn(ca, hval[a], hval[b]);
+            ++a;
+            --b;
+        }
+    }
+}
+
+__global__ void fold_count_kernel(int64_t Mh, int N, const int64_t* __restrict__ hrp,
+                                  const int32_t* __restrict__ hcol, const double* __restrict__ hval,
+                                  int32_t* __restrict__ cnt) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= Mh) return;
+    int n = 0;
+    for_each_folded(hcol, hval, hrp[i], hrp[i + 1], N, [&](int, double, double) { ++n; });
+    cnt[i] = n;
+}
+
+// Exclusive scan of cnt[0..n) into out[0..n]; out[n] = total.
+__global__ void scan_tiles_kernel(const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                                  int32_t* __restrict__ tile_sums, int64_t n) {
+    __shared__ int32_t warp_tot[kScanThreads / 32];
+    const int64_t base = blockIdx.x * (int64_t)kScanTile + threadIdx.x * (int64_t)kScanItems;
+    int32_t v[kScanItems];
+    int32_t run = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0;
+        run += v[k];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t incl = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = warp_tot[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        warp_tot[lane] = w;  // inclusive
+    }
+    __syncthreads();
+    int32_t excl = incl - run + (warp > 0 ? warp_tot[warp - 1] : 0);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = excl;
+        excl += v[k];
+    }
+    if (threadIdx.x == kScanThreads - 1) tile_sums[blockIdx.x] = warp_tot[31];
+}
+
+__global__ void scan_tile_sums_kernel(int32_t* __restrict__ tile_sums, int ntiles) {
+    // One CTA: exclusive scan of the tile sums, in chunks carried forward.
+    __shared__ int32_t warp_tot[32];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int b0 = 0; b0 < ntiles; b0 += blockDim.x) {
+        const int idx = b0 + threadIdx.x;
+        const int32_t v = idx < ntiles ? tile_sums[idx] : 0;
+        int32_t incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int32_t w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                int32_t t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
+            }
+            warp_tot[lane] = w;
+        }
+        __syncthreads();
+        const int32_t excl = carry + incl - v + (warp > 0 ? warp_tot[warp - 1] : 0);
+        if (idx < ntiles) tile_sums[idx] = excl;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += warp_tot[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tile_sums[ntiles] = carry;
+}
+
+__global__ void scan_add_kernel(int32_t* __restrict__ out, const int32_t* __restrict__ tile_sums, int64_t n,
+                                int ntiles) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] += tile_sums[i / kScanTile];
+    if (i == 0) out[n] = tile_sums[ntiles];
+}
+
+int exclusive_scan(const int32_t* in, int32_t* out, int32_t* tile_sums, int64_t n, cudaStream_t st) {
+    const int ntiles = (int)((n + kScanTile - 1) / kScanTile);
+    if (ntiles == 0) {
+        cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int32_t), st);
+        return e == cudaSuccess ? SPLITSART_OK : cuda_fail(e, "scan");
+    }
+    scan_tiles_kernel<<<ntiles, kScanThreads, 0, st>>>(in, out, tile_sums, n);
+    scan_tile_sums_kernel<<<1, 1024, 0, st>>>(tile_sums, ntiles);
+    scan_add_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, tile_sums, n, ntiles);
+    return SPLITSART_OK;
+}
+
+template <class T>
+__device__ __forceinline__ void store_pair(typename T::Pair* p, double a1, double a2, float s1, float s2,
+                                           double& d1, double& d2) {
+    if constexpr (T::kDtype == SPLITSART_F64) {
+        *p = make_double2(a1, a2);
+        d1 = a1;
+        d2 = a2;
+    } else if constexpr (T::kDtype == SPLITSART_F32) {
+        const float f1 = (float)a1, f2 = (float)a2;
+        *p = make_float2(f1, f2);
+        d1 = f1;
+        d2 = f2;
+    } else {
+        // Codes q = round(a / s), with the division and the rounding in FP32.
+        const float q1 = s1 > 0.f ? __fdiv_rn((float)a1, s1) : 0.f;
+        const float q2 = s2 > 0.f ? __fdiv_rn((float)a2, s2) : 0.f;
+        const typename T::Pair q = T::encode(q1, q2);
+        *p = q;
+        float c1, c2;
+        T::decode(q, c1, c2);
+        d1 = (double)s1 * (double)c1;  // exact: 24-bit x 11-bit mantissas
+        d2 = (double)s2 * (double)c2;
+    }
+}
+
+template <class T>
+__global__ void fold_fill_kernel(int64_t Mh, int N, const int64_t* __restrict__ hrp,
+                                 const int32_t* __restrict__ hcol, const double* __restrict__ hval,
+                                 const int32_t* __restrict__ frp, int32_t* __restrict__ col,
+                                 typename T::Pair* __restrict__ val, double2* __restrict__ Rsum,
+                                 typename T::Norm2* __restrict__ invR, float2* __restrict__ scale,
+                                 FoldStats* __restrict__ stats) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= Mh) return;
+    const int64_t e0 = hrp[i], e1 = hrp[i + 1];
+    float s1 = 0.f, s2 = 0.f;
+    if constexpr (T::kQuant) {
+        double m1 = 0.0, m2 = 0.0;
+        for_each_folded(hcol, hval, e0, e1, N, [&](int, double wd, double wr) {
+            m1 = fmax(m1, fabs(wd - wr));
+            m2 = fmax(m2, fabs(wd + wr));
+        });
+        s1 = (float)m1;
+        s2 = (float)m2;
+        scale[i] = make_float2(s1, s2);
+    }
+    int32_t out = frp[i];
+    double R1 = 0.0, R2 = 0.0;
+    long long zeros = 0;
+    for_each_folded(hcol, hval, e0, e1, N, [&](int c, double wd, double wr) {
+        const double a1 = wd - wr, a2 = wd + wr;
+        zeros += (a1 == 0.0);
+        col[out] = c;
+        double d1, d2;
+        store_pair<T>(&val[out], a1, a2, s1, s2, d1, d2);
+        R1 += fabs(d1);
+        R2 += fabs(d2);
+        ++out;
+    });
+    Rsum[i] = make_double2(R1, R2);
+    using N2 = typename T::Norm2;
+    using NS = decltype(N2{}.x);
+    invR[i] = N2{(NS)(R1 > 0.0 ? 1.0 / R1 : 0.0), (NS)(R2 > 0.0 ? 1.0 / R2 : 0.0)};
+    if (out == frp[i]) atomicAdd(reinterpret_cast<unsigned long long*>(&stats->empty_rows), 1ULL);
+    if (zeros) atomicAdd(reinterpret_cast<unsigned long long*>(&stats->exact_zeros), (unsigned long long)zeros);
+    if (i == Mh - 1) stats->S = frp[Mh];
+}
+
+__global__ void csc_count_kernel(const int32_t* __restrict__ frp, int64_t Mh, int64_t cap,
+                                 const int32_t* __restrict__ col, int32_t* __restrict__ ccnt) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= cap || e >= frp[Mh]) return;
+    atomicAdd(&ccnt[col[e]], 1);
+}
+
+template <class T>
+__global__ void csc_place_kernel(int64_t Mh, const int32_t* __restrict__ frp, const int32_t* __restrict__ col,
+                                 const typename T::Pair* __restrict__ val, const int32_t* __restrict__ cp,
+                                 int32_t* __restrict__ cursor, int32_t* __restrict__ row,
+                                 typename T::Pair* __restrict__ valT) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= Mh) return;
+    for (int32_t e = frp[i]; e < frp[i + 1]; ++e) {
+        const int32_t c = col[e];
+        const int32_t pos = cp[c] + atomicAdd(&cursor[c], 1);
+        row[pos] = (int32_t)i;
+        valT[pos] = val[e];
+    }
+}
+
+// Sort each column's entries by row (insertion sort; columns are short), then
+// take the absolute column sums in that fixed order.
+template <class T>
+__global__ void csc_sort_colsum_kernel(int64_t Nh, const int32_t* __restrict__ cp, int32_t* __restrict__ row,
+                                       typename T::Pair* __restrict__ valT, const float2* __restrict__ scale,
+                                       double2* __restrict__ Csum, typename T::Norm2* __restrict__ invC) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= Nh) return;
+    const int32_t b = cp[j], e = cp[j + 1];
+    for (int32_t k = b + 1; k < e; ++k) {
+        const int32_t r = row[k];
+        const typename T::Pair v = valT[k];
+        int32_t m = k - 1;
+        while (m >= b && row[m] > r) {
+            row[m + 1] = row[m];
+            valT[m + 1] = valT[m];
+            --m;
+        }
+        row[m + 1] = r;
+        valT[m + 1] = v;
+    }
+    double C1 = 0.0, C2 = 0.0;
+    for (int32_t k = b; k < e; ++k) {
+        typename T::Acc a1, a2;
+        T::decode(valT[k], a1, a2);
+        double d1 = a1, d2 = a2;
+        if constexpr (T::kQuant) {
+            const float2 s = scale[row[k]];
+            d1 = (double)s.x * d1;
+            d2 = (double)s.y * d2;
+        }
+        C1 += fabs(d1);
+        C2 += fabs(d2);
+    }
+    Csum[j] = make_double2(C1, C2);
+    using N2 = typename T::Norm2;
+    using NS = decltype(N2{}.x);
+    invC[j] = N2{(NS)(C1 > 0.0 ? 1.0 / C1 : 0.0), (NS)(C2 > 0.0 ? 1.0 / C2 : 0.0)};
+}
+
+template <class T>
+int fold_typed(splitsart_system* s, cudaStream_t st) {
+    using Pair = typename T::Pair;
+    using N2 = typename T::Norm2;
+    const int64_t Mh = s->Mh, Nh = s->Nh;
+    const int N = (int)s->N;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(s->stats, 0, sizeof(FoldStats), st)) != cudaSuccess) return cuda_fail(e, "fold memset");
+    if (Mh > 0) fold_count_kernel<<<(unsigned)((Mh + 255) / 256), 256, 0, st>>>(Mh, N, s->hrp, s->hcol, s->hval, s->cnt);
+    int rc = exclusive_scan(s->cnt, s->rp, s->scan_tmp, Mh, st);
+    if (rc) return rc;
+    if (Mh > 0)
+        fold_fill_kernel<T><<<(unsigned)((Mh + 127) / 128), 128, 0, st>>>(
+            Mh, N, s->hrp, s->hcol, s->hval, s->rp, s->col, (Pair*)s->val, s->Rsum, (N2*)s->invR, s->scale,
+            s->stats);
+    // CSC.
+    if ((e = cudaMemsetAsync(s->cnt, 0, sizeof(int32_t) * (Nh + 1), st)) != cudaSuccess)
+        return cuda_fail(e, "fold memset");
+    if (s->nnz_half > 0)
+        csc_count_kernel<<<(unsigned)((s->nnz_half + 255) / 256), 256, 0, st>>>(s->rp, Mh, s->nnz_half, s->col,
+                                                                                 s->cnt);
+    rc = exclusive_scan(s->cnt, s->cp, s->scan_tmp, Nh, st);
+    if (rc) return rc;
+    if ((e = cudaMemsetAsync(s->cnt, 0, sizeof(int32_t) * (Nh + 1), st)) != cudaSuccess)
+        return cuda_fail(e, "fold memset");
+    if (Mh > 0)
+        csc_place_kernel<T><<<(unsigned)((Mh + 127) / 128), 128, 0, st>>>(Mh, s->rp, s->col, (const Pair*)s->val,
+                                                                          s->cp, s->cnt, s->row, (Pair*)s->valT);
+    if (Nh > 0)
+        csc_sort_colsum_kernel<T><<<(unsigned)((Nh + 127) / 128), 128, 0, st>>>(
+            Nh, s->cp, s->row, (Pair*)s->valT, s->scale, s->Csum, (N2*)s->invC);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "fold launch");
+    return SPLITSART_OK;
+}
+
+// ---- vector kernels ----
+
+__device__ __forceinline__ int64_t image_index(int64_t j, int nx, int nz) {
+    const int64_t c = j / nz, q = j % nz;
+    const int64_t r = (c & 1) ? (nz - 1 - q) : q;
+    return r * nx + c;
+}
+
+template <class V, class V2>
+__global__ void fold_rhs_kernel(int64_t M, const V* __restrict__ p, V2* __restrict__ p12) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= M / 2) return;
+    const V a = p[i], b = p[M - 1 - i];
+    p12[i] = V2{a - b, a + b};
+}
+
+template <class V, class V2>
+__global__ void fold_image_kernel(int64_t N, int layout, int nx, int nz, const V* __restrict__ f,
+                                  V2* __restrict__ f12) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= N / 2) return;
+    const int64_t jm = N - 1 - j;
+    const int64_t a_idx = layout == SPLITSART_LAYOUT_IMAGE ? image_index(j, nx, nz) : j;
+    const int64_t b_idx = layout == SPLITSART_LAYOUT_IMAGE ? image_index(jm, nx, nz) : jm;
+    const V a = f[a_idx], b = f[b_idx];
+    f12[j] = V2{a - b, a + b};
+}
+
+// Theorem 1, Eq. (5).
+template <class V, class V2>
+__global__ void recombine_kernel(int64_t N, int layout, int nx, int nz, const V2* __restrict__ f12,
+                                 V* __restrict__ f) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= N / 2) return;
+    const V2 v = f12[j];
+    const int64_t jm = N - 1 - j;
+    const int64_t a_idx = layout == SPLITSART_LAYOUT_IMAGE ? image_index(j, nx, nz) : j;
+    const int64_t b_idx = layout == SPLITSART_LAYOUT_IMAGE ? image_index(jm, nx, nz) : jm;
+    f[a_idx] = (v.y + v.x) / V(2);
+    f[b_idx] = (v.y - v.x) / V(2);
+}
+
+// q = (A1 f1, A2 f2): one warp per folded row.
+template <class T>
+__global__ void spmv_pairs_kernel(int64_t Mh, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                  const typename T::Pair* __restrict__ val, const float2* __restrict__ scale,
+                                  const typename T::Vec2* __restrict__ f12, typename T::Vec2* __restrict__ q12) {
+    using Acc = typename T::Acc;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= Mh) return;
+    Acc s1 = 0, s2 = 0;
+    for (int32_t e = rp[w] + lane; e < rp[w + 1]; e += 32) {
+        Acc a1, a2;
+        T::decode(val[e], a1, a2);
+        const typename T::Vec2 fv = f12[col[e]];
+        s1 += a1 * fv.x;
+        s2 += a2 * fv.y;
+    }
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (lane == 0) {
+        if constexpr (T::kQuant) {
+            const float2 sc = scale[w];
+            s1 *= sc.x;
+            s2 *= sc.y;
+        }
+        q12[w] = typename T::Vec2{s1, s2};
+    }
+}
+
+// p_i = (q2 + q1)/2, p_{M-1-i} = (q2 - q1)/2: the fold of p, inverted.
+template <class V, class V2>
+__global__ void unfold_rays_kernel(int64_t M, const V2* __restrict__ q12, V* __restrict__ p) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= M / 2) return;
+    const V2 q = q12[i];
+    p[i] = (q.y + q.x) / V(2);
+    p[M - 1 - i] = (q.y - q.x) / V(2);
+}
+
+template <class T>
+int project_typed(splitsart_system* s, const void* f, int layout, void* p, cudaStream_t st) {
+    using V = typename T::Acc;
+    using V2 = typename T::Vec2;
+    const int64_t Nh = s->Nh, Mh = s->Mh;
+    if (Nh > 0)
+        fold_image_kernel<V, V2><<<(unsigned)((Nh + 255) / 256), 256, 0, st>>>(s->N, layout, s->nx, s->nz,
+                                                                              (const V*)f, (V2*)s->tmp_f12);
+    if (Mh > 0) {
+        spmv_pairs_kernel<T><<<(unsigned)((Mh * 32 + 255) / 256), 256, 0, st>>>(
+            Mh, s->rp, s->col, (const typename T::Pair*)s->val, s->scale, (const V2*)s->tmp_f12, (V2*)s->tmp_q12);
+        unfold_rays_kernel<V, V2><<<(unsigned)((Mh + 255) / 256), 256, 0, st>>>(s->M, (const V2*)s->tmp_q12, (V*)p);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SPLITSART_OK : cuda_fail(e, "project launch");
+}
+
+}  // namespace
+
+int run_fold(splitsart_system* s, cudaStream_t st) {
+    switch (s->dtype) {
+        case SPLITSART_F64: return fold_typed<TF64>(s, st);
+        case SPLITSART_F32: return fold_typed<TF32>(s, st);
+        case SPLITSART_BF16: return fold_typed<TBF16>(s, st);
+        case SPLITSART_F16: return fold_typed<TF16>(s, st);
+    }
+    return fail(SPLITSART_ERR_ARG, "fold: unknown dtype %d", s->dtype);
+}
+
+int run_fold_rhs(const splitsart_system* s, const void* p, void* p12, cudaStream_t st) {
+    const int64_t Mh = s->Mh;
+    if (Mh == 0) return SPLITSART_OK;
+    const unsigned g = (unsigned)((Mh + 255) / 256);
+    if (s->dtype == SPLITSART_F64) fold_rhs_kernel<double, double2><<<g, 256, 0, st>>>(s->M, (const double*)p, (double2*)p12);
+    else fold_rhs_kernel<float, float2><<<g, 256, 0, st>>>(s->M, (const float*)p, (float2*)p12);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SPLITSART_OK : cuda_fail(e, "fold_rhs launch");
+}
+
+int run_fold_image(const splitsart_system* s, const void* f, int layout, void* f12, cudaStream_t st) {
+    const int64_t Nh = s->Nh;
+    if (Nh == 0) return SPLITSART_OK;
+    const unsigned g = (unsigned)((Nh + 255) / 256);
+    if (s->dtype == SPLITSART_F64)
+        fold_image_kernel<double, double2><<<g, 256, 0, st>>>(s->N, layout, s->nx, s->nz, (const double*)f, (double2*)f12);
+    else
+        fold_image_kernel<float, float2><<<g, 256, 0, st>>>(s->N, layout, s->nx, s->nz, (const float*)f, (float2*)f12);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SPLITSART_OK : cuda_fail(e, "fold_image launch");
+}
+
+int run_recombine(const splitsart_system* s, const void* f12, void* f, int layout, cudaStream_t st) {
+    const int64_t Nh = s->Nh;
+    if (Nh == 0) return SPLITSART_OK;
+    const unsigned g = (unsigned)((Nh + 255) / 256);
+    if (s->dtype == SPLITSART_F64)
+        recombine_kernel<double, double2><<<g, 256, 0, st>>>(s->N, layout, s->nx, s->nz, (const double2*)f12, (double*)f);
+    else
+        recombine_kernel<float, float2><<<g, 256, 0, st>>>(s->N, layout, s->nx, s->nz, (const float2*)f12, (float*)f);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SPLITSART_OK : cuda_fail(e, "recombine launch");
+}
+
+int run_project(splitsart_system* s, const void* f, int layout, void* p, cudaStream_t st) {
+    switch (s->dtype) {
+        case SPLITSART_F64: return project_typed<TF64>(s, f, layout, p, st);
+        case SPLITSART_F32: return project_typed<TF32>(s, f, layout, p, st);
+        case SPLITSART_BF16: return project_typed<TBF16>(s, f, layout, p, st);
+        case SPLITSART_F16: return project_typed<TF16>(s, f, layout, p, st);
+    }
+    return fail(SPLITSART_ERR_ARG, "project: unknown dtype %d", s->dtype);
+}
+
+}  // namespace splitsart

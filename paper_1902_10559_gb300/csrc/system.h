@@ -1,0 +1,86 @@
+// Internal layout of a folded system on the device. Shared by the library's
+// translation units; not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "host_common.h"
+
+namespace splitsart {
+
+struct LaunchCtl;
+
+// Device-side counters written by the fold.
+struct FoldStats {
+    long long S;            // folded pattern size
+    long long empty_rows;   // folded rows without entries
+    long long exact_zeros;  // a1 == 0 by cancellation
+    long long pad;
+};
+
+// Result of one solve, written by CTA 0 of the persistent launch.
+struct SolveResultDev {
+    int iters;
+    int status;
+    double rho, rr, pp;
+};
+
+// Upper bound on grid-reduction partials (CTAs of one persistent launch).
+constexpr int kMaxCtas = 4096;
+
+}  // namespace splitsart
+
+struct splitsart_system {
+    int64_t M = 0, N = 0, Mh = 0, Nh = 0, nnz_half = 0;
+    int dtype = 0;
+    int nx = 0, nz = 0;
+    int64_t S = -1;  // host copy, read lazily
+    int64_t device_bytes = 0;
+    cudaStream_t last = nullptr;
+
+    // Uploaded first-half rows of A (FP64).
+    int64_t* hrp = nullptr;
+    int32_t* hcol = nullptr;
+    double* hval = nullptr;
+
+    // Folded CSR (capacity nnz_half; used length S).
+    int32_t* rp = nullptr;   // Mh + 1
+    int32_t* col = nullptr;  // S
+    void* val = nullptr;     // S pairs, storage by dtype
+    // Folded CSC.
+    int32_t* cp = nullptr;   // Nh + 1
+    int32_t* row = nullptr;  // S
+    void* valT = nullptr;    // S pairs
+    // Normalisers: raw absolute sums (double2) and reciprocals (storage by dtype).
+    double2* Rsum = nullptr;  // Mh
+    double2* Csum = nullptr;  // Nh
+    void* invR = nullptr;     // Mh pairs
+    void* invC = nullptr;     // Nh pairs
+    float2* scale = nullptr;  // Mh (BF16/F16 only)
+
+    // Scratch.
+    int32_t* cnt = nullptr;          // max(Mh, Nh) + 1 counters
+    int32_t* scan_tmp = nullptr;     // block sums of the scan
+    splitsart::FoldStats* stats = nullptr;
+    void* u12 = nullptr;             // Mh pairs (vector type)
+    void* tmp_f12 = nullptr;         // Nh pairs (vector type), projection
+    void* tmp_q12 = nullptr;         // Mh pairs (vector type), projection
+    double* partials = nullptr;      // 2 * kMaxCtas
+    splitsart::LaunchCtl* ctl = nullptr;
+    splitsart::SolveResultDev* result = nullptr;
+    void* base = nullptr;            // single device allocation holding all of the above
+};
+
+namespace splitsart {
+// Defined in fold.cu.
+int run_fold(splitsart_system* s, cudaStream_t st);
+int run_fold_rhs(const splitsart_system* s, const void* p, void* p12, cudaStream_t st);
+int run_fold_image(const splitsart_system* s, const void* f, int layout, void* f12, cudaStream_t st);
+int run_recombine(const splitsart_system* s, const void* f12, void* f, int layout, cudaStream_t st);
+int run_project(splitsart_system* s, const void* f, int layout, void* p, cudaStream_t st);
+// Defined in sart.cu.
+int run_solve(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o, cudaStream_t st);
+int cuda_fail(cudaError_t e, const char* what);
+}  // namespace splitsart

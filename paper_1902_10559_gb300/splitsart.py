@@ -1,0 +1,295 @@
+"""Thin Python binding over libsplitsart.so, the C ABI declared in include/splitsart.h.
+
+This module only marshals arguments. Every step of the method runs in the
+library's CUDA kernels. Device buffers are torch CUDA tensors, passed by
+pointer, and streams are torch streams. If the library has not been built, the
+first call raises. There is no fallback.
+
+The names follow the C ABI without the ``splitsart_`` prefix.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsplitsart.so")
+
+F64, F32, BF16, F16 = 0, 1, 2, 3
+LAYOUT_SNAKE, LAYOUT_IMAGE = 0, 1
+DTYPE_NAMES = {"f64": F64, "f32": F32, "bf16": BF16, "f16": F16}
+
+OK = 0
+ERR_ARG, ERR_ODD_DIM, ERR_ASYMMETRIC, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_STATE, ERR_NONFINITE = range(-1, -9, -1)
+
+
+class GeometryParams(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("nz", ctypes.c_int32), ("W", ctypes.c_double), ("H", ctypes.c_double),
+                ("z0", ctypes.c_double), ("K", ctypes.c_int32), ("gamma_deg", ctypes.c_double),
+                ("R", ctypes.c_double), ("nb", ctypes.c_int32), ("D", ctypes.c_double)]
+
+
+class SystemInfo(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int64), ("N", ctypes.c_int64), ("Mh", ctypes.c_int64), ("Nh", ctypes.c_int64),
+                ("nnz_half", ctypes.c_int64), ("S", ctypes.c_int64), ("empty_rows", ctypes.c_int64),
+                ("exact_zeros", ctypes.c_int64), ("dtype", ctypes.c_int32), ("nx", ctypes.c_int32),
+                ("nz", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int32), ("lambda_", ctypes.c_double), ("tol", ctypes.c_double),
+                ("check_every", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("lanes_per_col", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("timeout_ms", ctypes.c_double),
+                ("inject_barrier_fault", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("rho", ctypes.c_double),
+                ("rr", ctypes.c_double), ("pp", ctypes.c_double)]
+
+
+class SplitSartError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"splitsart error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+# Every symbol the header declares, with its argument and result types.
+_P = ctypes.c_void_p
+_SIGS = {
+    "splitsart_make_geometry": ([ctypes.POINTER(GeometryParams), ctypes.POINTER(_P)], ctypes.c_int),
+    "splitsart_make_geometry_from_csr": ([ctypes.c_int64, ctypes.c_int64, _P, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "splitsart_geometry_info": ([_P, _P, _P, _P], ctypes.c_int),
+    "splitsart_geometry_export": ([_P, _P, _P, _P], ctypes.c_int),
+    "splitsart_geometry_destroy": ([_P], None),
+    "splitsart_fold_system": ([_P, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "splitsart_refold": ([_P, _P], ctypes.c_int),
+    "splitsart_system_info_get": ([_P, ctypes.POINTER(SystemInfo)], ctypes.c_int),
+    "splitsart_system_export": ([_P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "splitsart_system_export_csc": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "splitsart_system_destroy": ([_P], None),
+    "splitsart_fold_rhs": ([_P, _P, _P, _P], ctypes.c_int),
+    "splitsart_fold_image": ([_P, _P, ctypes.c_int, _P, _P], ctypes.c_int),
+    "splitsart_recombine": ([_P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
+    "splitsart_project": ([_P, _P, ctypes.c_int, _P, _P], ctypes.c_int),
+    "splitsart_solve": ([_P, _P, _P, ctypes.POINTER(SolveOpts), _P], ctypes.c_int),
+    "splitsart_solve_result": ([_P, ctypes.POINTER(SolveInfo)], ctypes.c_int),
+    "splitsart_last_error": ([ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
+    "splitsart_version": ([], ctypes.c_char_p),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsplitsart.so (built by ``paper_1902_10559_gb300.build``). Raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def declared_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(1024)
+    lib().splitsart_last_error(buf, 1024)
+    return buf.value.decode()
+
+
+def _check(rc: int) -> None:
+    if rc != OK:
+        raise SplitSartError(rc, last_error())
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _vec_dtype(dtype: int):
+    import torch
+    return torch.float64 if dtype == F64 else torch.float32
+
+
+def _dev_ptr(t, numel: int, dtype, name: str) -> int:
+    if not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous tensor")
+    if t.numel() != numel:
+        raise ValueError(f"{name}: expected {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+class Geometry:
+    """The first M/2 rows of A, on the host. Wraps a ``splitsart_geometry`` handle."""
+
+    def __init__(self, handle: int, params=None):
+        self._h = ctypes.c_void_p(handle)
+        self.params = params
+        M, N, nnz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().splitsart_geometry_info(self._h, ctypes.byref(M), ctypes.byref(N), ctypes.byref(nnz)))
+        self.M, self.N, self.nnz_half = M.value, N.value, nnz.value
+
+    def export(self):
+        """Return (row_ptr int64[Mh+1], col int32[nnz], val float64[nnz])."""
+        rp = np.zeros(self.M // 2 + 1, dtype=np.int64)
+        col = np.zeros(max(self.nnz_half, 1), dtype=np.int32)
+        val = np.zeros(max(self.nnz_half, 1), dtype=np.float64)
+        _check(lib().splitsart_geometry_export(self._h, rp.ctypes.data, col.ctypes.data, val.ctypes.data))
+        return rp, col[: self.nnz_half], val[: self.nnz_half]
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.splitsart_geometry_destroy(self._h)
+            self._h = None
+
+
+def make_geometry(g) -> Geometry:
+    """Build the geometry from an object with nx, nz, W, H, z0, K, gamma_deg, R, nb, D."""
+    p = GeometryParams(g.nx, g.nz, g.W, g.H, g.z0, g.K, g.gamma_deg, g.R, g.nb, g.D)
+    h = ctypes.c_void_p()
+    _check(lib().splitsart_make_geometry(ctypes.byref(p), ctypes.byref(h)))
+    return Geometry(h.value, g)
+
+
+def make_geometry_from_csr(M: int, N: int, row_ptr, col, val) -> Geometry:
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    c = np.ascontiguousarray(col, dtype=np.int32)
+    v = np.ascontiguousarray(val, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(lib().splitsart_make_geometry_from_csr(M, N, rp.ctypes.data, c.ctypes.data, v.ctypes.data, ctypes.byref(h)))
+    return Geometry(h.value)
+
+
+class System:
+    """Folded A1/A2 on the device. Wraps a ``splitsart_system`` handle."""
+
+    def __init__(self, handle: int, dtype: int, geometry: Geometry):
+        self._h = ctypes.c_void_p(handle)
+        self.dtype = dtype
+        self.geometry = geometry
+        self.M, self.N = geometry.M, geometry.N
+        self.Mh, self.Nh = self.M // 2, self.N // 2
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def vec_dtype(self):
+        return _vec_dtype(self.dtype)
+
+    def info(self) -> dict:
+        i = SystemInfo()
+        _check(lib().splitsart_system_info_get(self._h, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in SystemInfo._fields_}
+
+    def export(self, normalisers: bool = False):
+        """Return the folded CSR on the host: row_ptr, col, a1, a2 and, if asked, R[Mh,2] and C[Nh,2]."""
+        S = self.info()["S"]
+        rp = np.zeros(self.Mh + 1, dtype=np.int64)
+        col = np.zeros(max(S, 1), dtype=np.int32)
+        a1 = np.zeros(max(S, 1))
+        a2 = np.zeros(max(S, 1))
+        R = np.zeros((max(self.Mh, 1), 2)) if normalisers else None
+        C = np.zeros((max(self.Nh, 1), 2)) if normalisers else None
+        _check(lib().splitsart_system_export(self._h, rp.ctypes.data, col.ctypes.data, a1.ctypes.data, a2.ctypes.data,
+                                             R.ctypes.data if normalisers else None,
+                                             C.ctypes.data if normalisers else None))
+        out = {"row_ptr": rp, "col": col[:S], "a1": a1[:S], "a2": a2[:S]}
+        if normalisers:
+            out["R"], out["C"] = R[: self.Mh], C[: self.Nh]
+        return out
+
+    def export_csc(self):
+        S = self.info()["S"]
+        cp = np.zeros(self.Nh + 1, dtype=np.int64)
+        row = np.zeros(max(S, 1), dtype=np.int32)
+        a1 = np.zeros(max(S, 1))
+        a2 = np.zeros(max(S, 1))
+        _check(lib().splitsart_system_export_csc(self._h, cp.ctypes.data, row.ctypes.data, a1.ctypes.data,
+                                                 a2.ctypes.data))
+        return {"col_ptr": cp, "row": row[:S], "a1": a1[:S], "a2": a2[:S]}
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.splitsart_system_destroy(self._h)
+            self._h = None
+
+
+def fold_system(geometry: Geometry, dtype: int = F32, stream=None) -> System:
+    h = ctypes.c_void_p()
+    _check(lib().splitsart_fold_system(geometry._h, dtype, _stream_ptr(stream), ctypes.byref(h)))
+    return System(h.value, dtype, geometry)
+
+
+def refold(system: System, stream=None) -> None:
+    _check(lib().splitsart_refold(system.handle, _stream_ptr(stream)))
+
+
+def fold_rhs(system: System, p, p12, stream=None) -> None:
+    """p: vec[M] -> p12: vec[Mh, 2] (pairs (p1_i, p2_i))."""
+    vt = system.vec_dtype
+    _check(lib().splitsart_fold_rhs(system.handle, _dev_ptr(p, system.M, vt, "p"),
+                                    _dev_ptr(p12, 2 * system.Mh, vt, "p12"), _stream_ptr(stream)))
+
+
+def fold_image(system: System, f, f12, layout: int = LAYOUT_SNAKE, stream=None) -> None:
+    vt = system.vec_dtype
+    _check(lib().splitsart_fold_image(system.handle, _dev_ptr(f, system.N, vt, "f"), layout,
+                                      _dev_ptr(f12, 2 * system.Nh, vt, "f12"), _stream_ptr(stream)))
+
+
+def recombine(system: System, f12, f, layout: int = LAYOUT_SNAKE, stream=None) -> None:
+    vt = system.vec_dtype
+    _check(lib().splitsart_recombine(system.handle, _dev_ptr(f12, 2 * system.Nh, vt, "f12"),
+                                     _dev_ptr(f, system.N, vt, "f"), layout, _stream_ptr(stream)))
+
+
+def project(system: System, f, p, layout: int = LAYOUT_SNAKE, stream=None) -> None:
+    vt = system.vec_dtype
+    _check(lib().splitsart_project(system.handle, _dev_ptr(f, system.N, vt, "f"), layout,
+                                   _dev_ptr(p, system.M, vt, "p"), _stream_ptr(stream)))
+
+
+def solve_opts(max_iters: int, lam: float, tol: float = 0.0, check_every: int = 1, block_threads: int = 0,
+               ctas_per_sm: int = 0, lanes_per_col: int = 0, timeout_ms: float = 0.0,
+               inject_barrier_fault: bool = False) -> SolveOpts:
+    return SolveOpts(max_iters, lam, tol, check_every, block_threads, ctas_per_sm, lanes_per_col, 0, timeout_ms,
+                     int(inject_barrier_fault), 0)
+
+
+def solve(system: System, p12, f12, opts: SolveOpts, stream=None) -> None:
+    """Enqueue the persistent split-SART solve. f12 holds f^0 on entry and the result on exit."""
+    vt = system.vec_dtype
+    _check(lib().splitsart_solve(system.handle, _dev_ptr(p12, 2 * system.Mh, vt, "p12"),
+                                 _dev_ptr(f12, 2 * system.Nh, vt, "f12"), ctypes.byref(opts), _stream_ptr(stream)))
+
+
+def solve_result(system: System, raise_on_error: bool = True) -> dict:
+    info = SolveInfo()
+    rc = lib().splitsart_solve_result(system.handle, ctypes.byref(info))
+    if rc != OK and raise_on_error:
+        raise SplitSartError(rc, last_error())
+    return {"iters": info.iters, "status": info.status, "rho": info.rho, "rr": info.rr, "pp": info.pp}
+
+
+def version() -> str:
+    return lib().splitsart_version().decode()
