@@ -163,7 +163,13 @@ extern "C" int splitsart_fold_system(const splitsart_geometry* g, int dtype, voi
         {(void**)&s->invR, nb * Mh},
         {(void**)&s->invC, nb * Nh},
         {(void**)&s->scale, quant ? sizeof(float2) * Mh : 0},
+        {(void**)&s->nzr, sizeof(int32_t) * (Mh + 1)},
+        {(void**)&s->nzrp, sizeof(int32_t) * (Mh + 1)},
+        {(void**)&s->zr, sizeof(int32_t) * (Mh + 1)},
+        {(void**)&s->nzc, sizeof(int32_t) * (Nh + 1)},
+        {(void**)&s->nzcp, sizeof(int32_t) * (Nh + 1)},
         {(void**)&s->cnt, sizeof(int32_t) * mx},
+        {(void**)&s->flags, sizeof(int32_t) * mx},
         {(void**)&s->scan_tmp, sizeof(int32_t) * ntiles},
         {(void**)&s->stats, sizeof(FoldStats)},
         {(void**)&s->u12, vb * Mh},

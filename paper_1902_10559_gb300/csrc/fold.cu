@@ -290,6 +290,44 @@ __global__ void csc_sort_colsum_kernel(int64_t Nh, const int32_t* __restrict__ c
     invC[j] = N2{(NS)(C1 > 0.0 ? 1.0 / C1 : 0.0), (NS)(C2 > 0.0 ? 1.0 / C2 : 0.0)};
 }
 
+__global__ void nonempty_flags_kernel(int64_t n, const int32_t* __restrict__ ptr, int32_t* __restrict__ flags) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) flags[i] = ptr[i + 1] > ptr[i];
+}
+
+// Split 0..n-1 into the indices with entries (nzlist, with their pointers
+// nzptr) and those without (zlist). pos is the exclusive scan of the flags.
+// The order is increasing in both lists, so the result is deterministic.
+__global__ void compact_kernel(int64_t n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ pos,
+                               int32_t* __restrict__ nzlist, int32_t* __restrict__ nzptr, int32_t* __restrict__ zlist,
+                               int* __restrict__ n_nz, int* __restrict__ n_z) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (ptr[i + 1] > ptr[i]) {
+        nzlist[pos[i]] = (int32_t)i;
+        nzptr[pos[i]] = ptr[i];
+    } else if (zlist) {
+        zlist[i - pos[i]] = (int32_t)i;
+    }
+    if (i == 0) {
+        const int total = pos[n];
+        nzptr[total] = ptr[n];
+        *n_nz = total;
+        if (n_z) *n_z = (int)(n - total);
+    }
+}
+
+int compact(const int32_t* ptr, int64_t n, int32_t* flags, int32_t* pos, int32_t* tile_sums, int32_t* nzlist,
+            int32_t* nzptr, int32_t* zlist, int* n_nz, int* n_z, cudaStream_t st) {
+    if (n == 0) return SPLITSART_OK;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    nonempty_flags_kernel<<<g, 256, 0, st>>>(n, ptr, flags);
+    int rc = exclusive_scan(flags, pos, tile_sums, n, st);
+    if (rc) return rc;
+    compact_kernel<<<g, 256, 0, st>>>(n, ptr, pos, nzlist, nzptr, zlist, n_nz, n_z);
+    return SPLITSART_OK;
+}
+
 template <class T>
 int fold_typed(splitsart_system* s, cudaStream_t st) {
     using Pair = typename T::Pair;
@@ -305,6 +343,9 @@ int fold_typed(splitsart_system* s, cudaStream_t st) {
         fold_fill_kernel<T><<<(unsigned)((Mh + 127) / 128), 128, 0, st>>>(
             Mh, N, s->hrp, s->hcol, s->hval, s->rp, s->col, (Pair*)s->val, s->Rsum, (N2*)s->invR, s->scale,
             s->stats);
+    rc = compact(s->rp, Mh, s->flags, s->cnt, s->scan_tmp, s->nzr, s->nzrp, s->zr, &s->stats->n_nzr,
+                 &s->stats->n_zr, st);
+    if (rc) return rc;
     // CSC.
     if ((e = cudaMemsetAsync(s->cnt, 0, sizeof(int32_t) * (Nh + 1), st)) != cudaSuccess)
         return cuda_fail(e, "fold memset");
@@ -321,6 +362,8 @@ int fold_typed(splitsart_system* s, cudaStream_t st) {
     if (Nh > 0)
         csc_sort_colsum_kernel<T><<<(unsigned)((Nh + 127) / 128), 128, 0, st>>>(
             Nh, s->cp, s->row, (Pair*)s->valT, s->scale, s->Csum, (N2*)s->invC);
+    rc = compact(s->cp, Nh, s->flags, s->cnt, s->scan_tmp, s->nzc, s->nzcp, nullptr, &s->stats->n_nzc, nullptr, st);
+    if (rc) return rc;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "fold launch");
     return SPLITSART_OK;
 }

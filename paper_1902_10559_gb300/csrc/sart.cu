@@ -5,24 +5,34 @@
 //     r^k = p^s - A_s f^k,   u^k = r^k / R,   f^{k+1} = f^k + lambda (A_s^T u^k) / C,
 // where R and C are absolute row and column sums with 1/0 := 0. The two
 // systems are independent (Theorem 1). They are run together because they
-// share the index pattern: one pass over col/row indices feeds both.
+// share the index pattern: one pass over the col/row indices feeds both.
 //
-// One iteration is two grid-wide phases:
-//   forward:  one warp per folded row. It gathers the pair (f1, f2) at each
-//             column, reduces (A1 f1, A2 f2) with a fixed shuffle tree, and
-//             writes the pair u = r / R. ||r||^2 and ||p||^2 are summed in
-//             FP64 into per-CTA partials.
-//   barrier, then the stop test: every CTA sums the partials in the same
-//             order, so all CTAs take the same decision.
-//   back:     LPC lanes per column walk the CSC (rows ascending), gather u,
-//             reduce with a fixed tree, and update the pair f in place.
+// Work layout. One CTA per SM (1024 threads), launched cooperatively.
+// - Each CTA owns a contiguous range of the non-empty rows with about S/G
+//   entries, and likewise a range of the non-empty columns. Empty rows and
+//   columns were compacted away by the fold.
+// - A range is cut into tiles of at most TE entries that end on row
+//   (column) boundaries. The tile boundaries are computed once per launch.
+//
+// Per iteration:
+//   forward: for each tile, all threads stream the tile's col/value pairs
+//            with coalesced loads, gather the pair (f1, f2) at each column,
+//            and stage the products in shared memory. One warp per row then
+//            reduces its products (lane-strided, fixed shuffle tree) and
+//            writes u = r / R. ||r||^2 and ||p||^2 accumulate in FP64.
+//   barrier: the last CTA to arrive sums the per-CTA norm partials in a
+//            fixed order and publishes rho. All CTAs take the same stop
+//            decision.
+//   back:    the same tiling over the CSC (rows ascending within a column).
+//            It gathers u. LPC lanes reduce each column and update f in place.
 //   barrier.
-// No atomics touch values, so results are bitwise reproducible for a given
-// launch shape.
+// Each row's and each column's sum is formed in an order that depends on
+// neither the tiling nor the grid, so f is bitwise reproducible across
+// launch shapes with the same LPC. No atomics touch values.
 //
-// Vectors rewritten during the launch (f12 and u12) are read through L2
-// (ld.global.cg), so a CTA never sees a stale L1 copy. The matrix, p, and
-// the normalisers use the read-only path.
+// Vectors rewritten during the launch (f12, u12) are read through L2
+// (ld.global.cg), so a CTA never sees a stale L1 copy. The matrix, p and the
+// normalisers use the read-only path.
 #include <cstdio>
 
 #include "device_common.cuh"
@@ -32,12 +42,18 @@ namespace splitsart {
 
 namespace {
 
+constexpr int kMaxTiles = 1024;  // tiles per CTA and phase
+constexpr int kUnroll = 4;
+
 template <class T>
 struct SartArgs {
-    const int32_t* __restrict__ rp;
+    const int32_t* __restrict__ nzr;
+    const int32_t* __restrict__ nzrp;
+    const int32_t* __restrict__ zr;
+    const int32_t* __restrict__ nzc;
+    const int32_t* __restrict__ nzcp;
     const int32_t* __restrict__ col;
     const typename T::Pair* __restrict__ val;
-    const int32_t* __restrict__ cp;
     const int32_t* __restrict__ row;
     const typename T::Pair* __restrict__ valT;
     const typename T::Norm2* __restrict__ invR;
@@ -49,180 +65,313 @@ struct SartArgs {
     double* partials;  // [2 * gridDim.x]: (rr, pp) per CTA
     LaunchCtl* ctl;
     SolveResultDev* result;
-    int Mh, Nh;
+    const FoldStats* stats;
     int max_iters, check_every;
     double lambda, tol;
     unsigned long long timeout_ns;
     unsigned expected;  // CTAs the barrier waits for
+    int tile_entries;   // TE
 };
 
-constexpr int kUnroll = 4;
-
-// Forward projection of one row for both systems, by one warp.
-template <class T>
-__device__ __forceinline__ void row_dot(const SartArgs<T>& a, int i, int lane, typename T::Acc& s1,
-                                        typename T::Acc& s2) {
-    using Acc = typename T::Acc;
-    using V2 = typename T::Vec2;
-    const int e0 = __ldg(a.rp + i), e1 = __ldg(a.rp + i + 1);
-    s1 = 0;
-    s2 = 0;
-    for (int base = e0; base < e1; base += 32 * kUnroll) {
-        int c[kUnroll];
-        typename T::Pair v[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int e = base + u * 32 + lane;
-            if (e < e1) {
-                c[u] = ldg(a.col + e);
-                v[u] = ldg(a.val + e);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int e = base + u * 32 + lane;
-            if (e < e1) {
-                const V2 fv = ldcg(a.f12 + c[u]);
-                Acc a1, a2;
-                T::decode(v[u], a1, a2);
-                s1 += a1 * fv.x;
-                s2 += a2 * fv.y;
-            }
-        }
+// Warp-cooperative search: the first q in [lo, hi] with ptr[q] >= t, where
+// ptr is non-decreasing and q = hi if no probed index qualifies. Only indices
+// below hi are read. Each round probes 32 evenly spaced indices; the probes
+// below t form a prefix, so their count narrows the range 32-fold.
+__device__ __forceinline__ int warp_lower_bound(const int32_t* ptr, int lo, int hi, long long t, int lane) {
+    while (hi - lo > 32) {
+        const int step = (hi - lo + 31) / 32;
+        const int idx = lo + lane * step;
+        const bool below = idx < hi && (long long)__ldg(ptr + idx) < t;
+        const int c = __popc(__ballot_sync(0xffffffffu, below));
+        if (c == 0) return lo;
+        const int nlo = lo + (c - 1) * step + 1;
+        hi = min(lo + c * step, hi);
+        lo = nlo;
     }
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
+    const int idx = lo + lane;
+    const bool below = idx < hi && (long long)__ldg(ptr + idx) < t;
+    return lo + __popc(__ballot_sync(0xffffffffu, below));
+}
+
+// One warp: cut this CTA's share of [0, n) (balanced by the entry counts of
+// ptr[0..n]) into tiles of at most TE entries that end on boundaries. Lane 0
+// writes the boundaries to tiles[]. Returns the tile count, or -1 if more
+// than kMaxTiles would be needed.
+__device__ int plan_tiles(const int32_t* ptr, int n, int TE, int* tiles, int lane) {
+    const long long S = __ldg(ptr + n);
+    const long long G = gridDim.x, b = blockIdx.x;
+    const int q0 = warp_lower_bound(ptr, 0, n, S * b / G, lane);
+    const int q1 = (b == G - 1) ? n : warp_lower_bound(ptr, 0, n, S * (b + 1) / G, lane);
+    int nt = 0;
+    int q = q0;
+    while (q < q1) {
+        if (nt >= kMaxTiles) return -1;
+        if (lane == 0) tiles[nt] = q;
+        ++nt;
+        // Largest q' in (q, q1] with ptr[q'] <= ptr[q] + TE, and at least q + 1.
+        const long long lim = (long long)__ldg(ptr + q) + TE;
+        const int x = warp_lower_bound(ptr, q + 1, q1 + 1, lim + 1, lane);
+        q = max(q + 1, x - 1);
+    }
+    if (lane == 0) tiles[nt] = q1;
+    return nt;
 }
 
 template <class T, int LPC>
-__global__ void __launch_bounds__(256, 4) sart_persistent_kernel(SartArgs<T> a) {
+__global__ void __launch_bounds__(1024, 1) sart_persistent_kernel(SartArgs<T> a) {
     using Acc = typename T::Acc;
     using V2 = typename T::Vec2;
+    using Pair = typename T::Pair;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V2* prod = reinterpret_cast<V2*>(smem_raw);
+    __shared__ int s_rt[kMaxTiles + 1];
+    __shared__ int s_ct[kMaxTiles + 1];
+    __shared__ int s_nrt, s_nct;
     __shared__ double s_red[2][32];
-    __shared__ double s_rho[3];
 
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int nwarps_blk = blockDim.x >> 5;
-    const int gwarp = blockIdx.x * nwarps_blk + wib;
-    const int nwarps = gridDim.x * nwarps_blk;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int wib = tid >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int BD = blockDim.x;
+    const int TE = a.tile_entries;
     constexpr int kGroupsPerWarp = 32 / LPC;
     const int sub = lane % LPC;
     const Acc lam = (Acc)a.lambda;
 
+    // ---- launch prologue: tiles, and the empty rows' share of ||p||^2 ----
+    const int n_nzr = a.stats->n_nzr, n_nzc = a.stats->n_nzc, n_zr = a.stats->n_zr;
+    if (wib == 0) {
+        const int nt = plan_tiles(a.nzrp, n_nzr, TE, s_rt, lane);
+        if (lane == 0) {
+            s_nrt = nt;
+            if (nt < 0) atomicCAS(&a.ctl->err, 0, SPLITSART_ERR_ARG);
+        }
+    } else if (wib == 1) {
+        const int nt = plan_tiles(a.nzcp, n_nzc, TE, s_ct, lane);
+        if (lane == 0) {
+            s_nct = nt;
+            if (nt < 0) atomicCAS(&a.ctl->err, 0, SPLITSART_ERR_ARG);
+        }
+    }
+    double ppz = 0.0;  // sum of p1^2 + p2^2 over this CTA's share of the empty rows
+    {
+        const long long G = gridDim.x, b = blockIdx.x;
+        const int z0 = (int)(n_zr * b / G), z1 = (int)(n_zr * (b + 1) / G);
+        for (int z = z0 + tid; z < z1; z += BD) {
+            const V2 p = ldg(a.p12 + __ldg(a.zr + z));
+            ppz += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+        }
+        ppz = warp_sum(ppz);
+        if (lane == 0) s_red[0][wib] = ppz;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < nwarps; ++w) t += s_red[0][w];
+            ppz = t;  // meaningful in thread 0 only
+        }
+    }
     int barrier_no = 0;
+    if (!grid_barrier(a.ctl, a.expected, a.timeout_ns, barrier_no++)) return;
+    const int nrt = s_nrt, nct = s_nct;
+
     for (int k = 0;; ++k) {
         // ---- forward: r = p - A f, u = r / R, and the norm partials ----
         double rr = 0.0, pp = 0.0;
-        for (int i = gwarp; i < a.Mh; i += nwarps) {
-            Acc s1, s2;
-            row_dot<T>(a, i, lane, s1, s2);
-            if (lane == 0) {
-                const V2 p = ldg(a.p12 + i);
-                if constexpr (T::kQuant) {
-                    const float2 sc = ldg(a.scale + i);
-                    s1 *= sc.x;
-                    s2 *= sc.y;
+        for (int t = 0; t < nrt; ++t) {
+            const int qa = s_rt[t], qb = s_rt[t + 1];
+            const int ea = __ldg(a.nzrp + qa), eb = __ldg(a.nzrp + qb);
+            const int n = eb - ea;
+            const bool staged = n <= TE;
+            if (staged) {
+                for (int base = 0; base < n; base += BD * kUnroll) {
+                    int c[kUnroll];
+                    Pair v[kUnroll];
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        const int e = base + u * BD + tid;
+                        if (e < n) {
+                            c[u] = ldg(a.col + ea + e);
+                            v[u] = ldg(a.val + ea + e);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        const int e = base + u * BD + tid;
+                        if (e < n) {
+                            const V2 fv = ldcg(a.f12 + c[u]);
+                            Acc a1, a2;
+                            T::decode(v[u], a1, a2);
+                            prod[e] = V2{a1 * fv.x, a2 * fv.y};
+                        }
+                    }
                 }
-                const Acc r1 = p.x - s1, r2 = p.y - s2;
-                const typename T::Norm2 ir = ldg(a.invR + i);
-                V2 u;
-                if constexpr (T::kQuant) {
-                    // Back-projection reuses the codes, so fold the row scale into u.
-                    const float2 sc = ldg(a.scale + i);
-                    u.x = (Acc)((double)r1 * ir.x * (double)sc.x);
-                    u.y = (Acc)((double)r2 * ir.y * (double)sc.y);
-                } else {
-                    u.x = r1 * ir.x;
-                    u.y = r2 * ir.y;
-                }
-                stcg(a.u12 + i, u);
-                rr += (double)r1 * (double)r1 + (double)r2 * (double)r2;
-                pp += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+                __syncthreads();
             }
+            for (int q = qa + wib; q < qb; q += nwarps) {
+                const int i = __ldg(a.nzr + q);
+                const int lo = __ldg(a.nzrp + q) - ea, hi = __ldg(a.nzrp + q + 1) - ea;
+                V2 p{};
+                typename T::Norm2 ir{};
+                float2 sc{};
+                if (lane == 0) {
+                    p = ldg(a.p12 + i);
+                    ir = ldg(a.invR + i);
+                    if constexpr (T::kQuant) sc = ldg(a.scale + i);
+                }
+                Acc s1 = 0, s2 = 0;
+                if (staged) {
+                    for (int e = lo + lane; e < hi; e += 32) {
+                        const V2 pr = prod[e];
+                        s1 += pr.x;
+                        s2 += pr.y;
+                    }
+                } else {
+                    // A row longer than a tile: stream it straight from memory.
+                    for (int e = lo + lane; e < hi; e += 32) {
+                        const V2 fv = ldcg(a.f12 + ldg(a.col + ea + e));
+                        Acc a1, a2;
+                        T::decode(ldg(a.val + ea + e), a1, a2);
+                        s1 += a1 * fv.x;
+                        s2 += a2 * fv.y;
+                    }
+                }
+                s1 = warp_sum(s1);
+                s2 = warp_sum(s2);
+                if (lane == 0) {
+                    if constexpr (T::kQuant) {
+                        s1 *= sc.x;
+                        s2 *= sc.y;
+                    }
+                    const Acc r1 = p.x - s1, r2 = p.y - s2;
+                    V2 u;
+                    if constexpr (T::kQuant) {
+                        // The back-projection reuses the codes, so the row scale moves into u.
+                        u.x = (Acc)((double)r1 * ir.x * (double)sc.x);
+                        u.y = (Acc)((double)r2 * ir.y * (double)sc.y);
+                    } else {
+                        u.x = r1 * ir.x;
+                        u.y = r2 * ir.y;
+                    }
+                    stcg(a.u12 + i, u);
+                    rr += (double)r1 * (double)r1 + (double)r2 * (double)r2;
+                    pp += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+                }
+            }
+            __syncthreads();  // prod is reused by the next tile
         }
         if (lane == 0) {
             s_red[0][wib] = rr;
             s_red[1][wib] = pp;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double t0 = 0.0, t1 = 0.0;
-            for (int w = 0; w < nwarps_blk; ++w) {
+        if (tid == 0) {
+            double t0 = ppz, t1 = ppz;  // an empty row's residual is its p
+            for (int w = 0; w < nwarps; ++w) {
                 t0 += s_red[0][w];
                 t1 += s_red[1][w];
             }
             __stcg(a.partials + 2 * blockIdx.x, t0);
             __stcg(a.partials + 2 * blockIdx.x + 1, t1);
         }
-        if (!grid_barrier(a.ctl, a.expected, a.timeout_ns, barrier_no++)) return;
+        if (!grid_barrier(a.ctl, a.expected, a.timeout_ns, barrier_no++, a.partials)) return;
 
-        // ---- stop test ----
+        // ---- stop test on the published totals ----
         const bool last = (k >= a.max_iters);
-        const bool check = last || (k % a.check_every == 0);
-        if (check) {
-            if (wib == 0) {
-                double t0 = 0.0, t1 = 0.0;
-                for (int b = lane; b < (int)gridDim.x; b += 32) {
-                    t0 += __ldcg(a.partials + 2 * b);
-                    t1 += __ldcg(a.partials + 2 * b + 1);
-                }
-                t0 = warp_sum(t0);
-                t1 = warp_sum(t1);
-                if (lane == 0) {
-                    s_rho[0] = t0;
-                    s_rho[1] = t1;
-                    s_rho[2] = t1 > 0.0 ? sqrt(t0 / t1) : 0.0;
-                }
-            }
-            __syncthreads();
-            const double rho = s_rho[2];
+        if (last || (k % a.check_every == 0)) {
+            const double trr = __ldcg(&a.ctl->sum0), tpp = __ldcg(&a.ctl->sum1);
+            const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
             if (last || rho <= a.tol) {
-                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                if (blockIdx.x == 0 && tid == 0) {
                     a.result->iters = k;
                     a.result->status = SPLITSART_OK;
                     a.result->rho = rho;
-                    a.result->rr = s_rho[0];
-                    a.result->pp = s_rho[1];
+                    a.result->rr = trr;
+                    a.result->pp = tpp;
                 }
                 return;
             }
         }
 
         // ---- back-projection and update: f += lambda (A^T u) / C ----
-        // The outer loop is warp-uniform, so every lane reaches the shuffles.
-        for (int jb = gwarp * kGroupsPerWarp; jb < a.Nh; jb += nwarps * kGroupsPerWarp) {
-            const int j = jb + lane / LPC;
-            Acc b1 = 0, b2 = 0;
-            if (j < a.Nh) {
-                const int e0 = __ldg(a.cp + j), e1 = __ldg(a.cp + j + 1);
-                for (int e = e0 + sub; e < e1; e += LPC) {
-                    const int r = ldg(a.row + e);
-                    const typename T::Pair v = ldg(a.valT + e);
-                    const V2 u = ldcg(a.u12 + r);
-                    Acc a1, a2;
-                    T::decode(v, a1, a2);
-                    b1 += a1 * u.x;
-                    b2 += a2 * u.y;
+        for (int t = 0; t < nct; ++t) {
+            const int qa = s_ct[t], qb = s_ct[t + 1];
+            const int ea = __ldg(a.nzcp + qa), eb = __ldg(a.nzcp + qb);
+            const int n = eb - ea;
+            const bool staged = n <= TE;
+            if (staged) {
+                for (int base = 0; base < n; base += BD * kUnroll) {
+                    int r[kUnroll];
+                    Pair v[kUnroll];
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        const int e = base + u * BD + tid;
+                        if (e < n) {
+                            r[u] = ldg(a.row + ea + e);
+                            v[u] = ldg(a.valT + ea + e);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        const int e = base + u * BD + tid;
+                        if (e < n) {
+                            const V2 uv = ldcg(a.u12 + r[u]);
+                            Acc a1, a2;
+                            T::decode(v[u], a1, a2);
+                            prod[e] = V2{a1 * uv.x, a2 * uv.y};
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+            // Warp-uniform loop over groups of columns, so every lane reaches the shuffles.
+            for (int qb0 = qa + wib * kGroupsPerWarp; qb0 < qb; qb0 += nwarps * kGroupsPerWarp) {
+                const int q = qb0 + lane / LPC;
+                Acc b1 = 0, b2 = 0;
+                int j = -1;
+                if (q < qb) {
+                    j = __ldg(a.nzc + q);
+                    const int lo = __ldg(a.nzcp + q) - ea, hi = __ldg(a.nzcp + q + 1) - ea;
+                    if (staged) {
+                        for (int e = lo + sub; e < hi; e += LPC) {
+                            const V2 pr = prod[e];
+                            b1 += pr.x;
+                            b2 += pr.y;
+                        }
+                    } else {
+                        for (int e = lo + sub; e < hi; e += LPC) {
+                            const V2 uv = ldcg(a.u12 + ldg(a.row + ea + e));
+                            Acc a1, a2;
+                            T::decode(ldg(a.valT + ea + e), a1, a2);
+                            b1 += a1 * uv.x;
+                            b2 += a2 * uv.y;
+                        }
+                    }
+                }
+                b1 = warp_sum(b1, LPC);
+                b2 = warp_sum(b2, LPC);
+                if (sub == 0 && j >= 0) {
+                    const typename T::Norm2 ic = ldg(a.invC + j);
+                    V2 f = ldcg(a.f12 + j);
+                    if constexpr (T::kQuant) {
+                        f.x += (Acc)((double)(lam * b1) * ic.x);
+                        f.y += (Acc)((double)(lam * b2) * ic.y);
+                    } else {
+                        f.x += lam * b1 * ic.x;
+                        f.y += lam * b2 * ic.y;
+                    }
+                    stcg(a.f12 + j, f);
                 }
             }
-            b1 = warp_sum(b1, LPC);
-            b2 = warp_sum(b2, LPC);
-            if (sub == 0 && j < a.Nh) {
-                const typename T::Norm2 ic = ldg(a.invC + j);
-                V2 f = ldcg(a.f12 + j);
-                if constexpr (T::kQuant) {
-                    f.x += (Acc)((double)(lam * b1) * ic.x);
-                    f.y += (Acc)((double)(lam * b2) * ic.y);
-                } else {
-                    f.x += lam * b1 * ic.x;
-                    f.y += lam * b2 * ic.y;
-                }
-                stcg(a.f12 + j, f);
-            }
+            __syncthreads();
         }
         if (!grid_barrier(a.ctl, a.expected, a.timeout_ns, barrier_no++)) return;
     }
+}
+
+template <class T>
+constexpr int default_tile_entries() {
+    return sizeof(typename T::Vec2) == 16 ? 8192 : 12288;
 }
 
 template <class T, int LPC>
@@ -235,11 +384,15 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (!coop) return fail(SPLITSART_ERR_CUDA, "solve: device lacks cooperative launch");
-    const int threads = o.block_threads > 0 ? o.block_threads : 256;
-    if (threads % 32 != 0 || threads > 256 || threads < LPC)
-        return fail(SPLITSART_ERR_ARG, "solve: block_threads must be a multiple of 32 in [32, 256]");
+    const int threads = o.block_threads > 0 ? o.block_threads : 1024;
+    if (threads % 32 != 0 || threads > 1024 || threads < 64)
+        return fail(SPLITSART_ERR_ARG, "solve: block_threads must be a multiple of 32 in [64, 1024]");
+    const int TE = default_tile_entries<T>();
+    const size_t dyn = sizeof(typename T::Vec2) * (size_t)TE;
+    e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return cuda_fail(e, "solve: shared memory attribute");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, dyn);
     if (e != cudaSuccess) return cuda_fail(e, "solve: occupancy");
     if (o.ctas_per_sm > 0 && o.ctas_per_sm < per_sm) per_sm = o.ctas_per_sm;
     int grid = nsm * per_sm;
@@ -247,10 +400,13 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
     if (grid < 1) return fail(SPLITSART_ERR_CUDA, "solve: kernel does not fit on an SM");
 
     SartArgs<T> a;
-    a.rp = s->rp;
+    a.nzr = s->nzr;
+    a.nzrp = s->nzrp;
+    a.zr = s->zr;
+    a.nzc = s->nzc;
+    a.nzcp = s->nzcp;
     a.col = s->col;
     a.val = (const typename T::Pair*)s->val;
-    a.cp = s->cp;
     a.row = s->row;
     a.valT = (const typename T::Pair*)s->valT;
     a.invR = (const typename T::Norm2*)s->invR;
@@ -262,8 +418,7 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
     a.partials = s->partials;
     a.ctl = s->ctl;
     a.result = s->result;
-    a.Mh = (int)s->Mh;
-    a.Nh = (int)s->Nh;
+    a.stats = s->stats;
     a.max_iters = o.max_iters;
     a.check_every = o.check_every > 0 ? o.check_every : 1;
     a.lambda = o.lambda;
@@ -271,13 +426,14 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
     const double tms = o.timeout_ms > 0 ? o.timeout_ms : 2000.0;
     a.timeout_ns = (unsigned long long)(tms * 1e6);
     a.expected = (unsigned)grid + (o.inject_barrier_fault ? 1u : 0u);
+    a.tile_entries = TE;
 
     if ((e = cudaMemsetAsync(s->ctl, 0, sizeof(LaunchCtl), st)) != cudaSuccess) return cuda_fail(e, "solve: memset");
     // A result the launch never writes (a timeout) reads back as iters = -1.
     if ((e = cudaMemsetAsync(s->result, 0xff, sizeof(SolveResultDev), st)) != cudaSuccess)
         return cuda_fail(e, "solve: memset");
     void* args[] = {&a};
-    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(threads), args, 0, st);
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(threads), args, dyn, st);
     if (e != cudaSuccess) return cuda_fail(e, "solve: cooperative launch");
     return SPLITSART_OK;
 }

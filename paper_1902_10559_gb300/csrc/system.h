@@ -18,6 +18,10 @@ struct FoldStats {
     long long empty_rows;   // folded rows without entries
     long long exact_zeros;  // a1 == 0 by cancellation
     long long pad;
+    int n_nzr;              // rows with entries
+    int n_nzc;              // columns with entries
+    int n_zr;               // rows without entries
+    int pad2;
 };
 
 // Result of one solve, written by CTA 0 of the persistent launch.
@@ -60,8 +64,16 @@ struct splitsart_system {
     void* invC = nullptr;     // Nh pairs
     float2* scale = nullptr;  // Mh (BF16/F16 only)
 
+    // Compacted index lists (entries of empty rows/columns are skipped by the solve).
+    int32_t* nzr = nullptr;   // rows with entries, increasing (n_nzr)
+    int32_t* nzrp = nullptr;  // rp of those rows, plus S at the end (n_nzr + 1)
+    int32_t* zr = nullptr;    // rows without entries (n_zr)
+    int32_t* nzc = nullptr;   // columns with entries (n_nzc)
+    int32_t* nzcp = nullptr;  // cp of those columns, plus S at the end (n_nzc + 1)
+
     // Scratch.
     int32_t* cnt = nullptr;          // max(Mh, Nh) + 1 counters
+    int32_t* flags = nullptr;        // max(Mh, Nh) + 1 scan scratch
     int32_t* scan_tmp = nullptr;     // block sums of the scan
     splitsart::FoldStats* stats = nullptr;
     void* u12 = nullptr;             // Mh pairs (vector type)
