@@ -285,6 +285,48 @@ typedef struct splitsart_solve_info {
  */
 int splitsart_solve_result(splitsart_system* sys, splitsart_solve_info* info);
 
+/*
+ * Allocation-free solve. The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc. Examples are a process that
+ * reserves all of its device memory at start-up and forbids allocation
+ * afterwards, and a plugin inside a host application that owns the GPU's
+ * memory budget. Such a caller cannot use splitsart_fold_system, which
+ * allocates. It can place a folded system in buffers of its own and solve it
+ * here.
+ *
+ * The call runs the same persistent SART kernel as splitsart_solve, on a
+ * plain folded FP32 system. It allocates nothing. Its working memory is one
+ * fixed array inside the library (a static __device__ array of about
+ * 0.6 MiB), which every GPU that loads the library holds until the process
+ * exits. The array holds:
+ * - the launch control block, the result, and the per-CTA norm partials;
+ * - u for at most 65536 folded rows.
+ * Larger systems (Mh > 65536) are rejected with SPLITSART_ERR_ARG; use
+ * splitsart_solve for them.
+ *
+ * Arguments, all device pointers owned by the caller:
+ * - rp_dev[Mh+1] int32, col_dev[S] int32, val_dev[S] float2 (a1, a2): the
+ *   folded CSR, with columns increasing within a row;
+ * - cp_dev[Nh+1] int32, row_dev[S] int32, valT_dev[S] float2: the folded CSC,
+ *   with rows increasing within a column;
+ * - invR_dev[Mh], invC_dev[Nh] float2: reciprocal absolute row and column
+ *   sums, 0 where a sum is 0;
+ * - p12_dev[Mh] float2, and f12_dev[Nh] float2 (in: f0, out: the result);
+ * - info_dev: device splitsart_solve_info, written when the call's work
+ *   completes. status is SPLITSART_ERR_TIMEOUT if a barrier wait ran out.
+ * `opts` is read as in splitsart_solve.
+ *
+ * The first call made with a device current looks up the array's device
+ * address on that device. Make that first call before any stream capture.
+ * Every call shares the one array and clears its control block on `stream`.
+ * Calls that overlap on the GPU (other streams, other host threads) race on
+ * the array and must be serialised by the caller.
+ */
+int splitsart_solve_static(int64_t Mh, int64_t Nh, const int32_t* rp_dev, const int32_t* col_dev, const void* val_dev,
+                           const int32_t* cp_dev, const int32_t* row_dev, const void* valT_dev, const void* invR_dev,
+                           const void* invC_dev, const void* p12_dev, void* f12_dev, const splitsart_solve_opts* opts,
+                           splitsart_solve_info* info_dev, void* stream);
+
 /* Copy the thread's last error message into buf (truncated, NUL-terminated). Returns its full length. */
 int splitsart_last_error(char* buf, size_t len);
 

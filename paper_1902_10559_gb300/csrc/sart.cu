@@ -33,7 +33,9 @@
 // Vectors rewritten during the launch (f12, u12) are read through L2
 // (ld.global.cg), so a CTA never sees a stale L1 copy. The matrix, p and the
 // normalisers use the read-only path.
+#include <cmath>
 #include <cstdio>
+#include <mutex>
 
 #include "device_common.cuh"
 #include "system.h"
@@ -71,6 +73,8 @@ struct SartArgs {
     unsigned long long timeout_ns;
     unsigned expected;  // CTAs the barrier waits for
     int tile_entries;   // TE
+    int direct_rows;    // kDirect only: Mh (nzrp = rp, row q is row q, no empty-row list)
+    int direct_cols;    // kDirect only: Nh (nzcp = cp, column q is column q)
 };
 
 // Warp-cooperative search: the first q in [lo, hi] with ptr[q] >= t, where
@@ -117,7 +121,9 @@ __device__ int plan_tiles(const int32_t* ptr, int n, int TE, int* tiles, int lan
     return nt;
 }
 
-template <class T, int LPC>
+// kDirect: the caller's plain folded CSR/CSC is used as is (no compacted
+// lists). Empty rows then pass through the row loop with no entries.
+template <class T, int LPC, bool kDirect = false>
 __global__ void __launch_bounds__(1024, 1) sart_persistent_kernel(SartArgs<T> a) {
     using Acc = typename T::Acc;
     using V2 = typename T::Vec2;
@@ -140,7 +146,9 @@ __global__ void __launch_bounds__(1024, 1) sart_persistent_kernel(SartArgs<T> a)
     const Acc lam = (Acc)a.lambda;
 
     // ---- launch prologue: tiles, and the empty rows' share of ||p||^2 ----
-    const int n_nzr = a.stats->n_nzr, n_nzc = a.stats->n_nzc, n_zr = a.stats->n_zr;
+    const int n_nzr = kDirect ? a.direct_rows : a.stats->n_nzr;
+    const int n_nzc = kDirect ? a.direct_cols : a.stats->n_nzc;
+    const int n_zr = kDirect ? 0 : a.stats->n_zr;
     if (wib == 0) {
         const int nt = plan_tiles(a.nzrp, n_nzr, TE, s_rt, lane);
         if (lane == 0) {
@@ -209,7 +217,7 @@ __global__ void __launch_bounds__(1024, 1) sart_persistent_kernel(SartArgs<T> a)
                 __syncthreads();
             }
             for (int q = qa + wib; q < qb; q += nwarps) {
-                const int i = __ldg(a.nzr + q);
+                const int i = kDirect ? q : __ldg(a.nzr + q);
                 const int lo = __ldg(a.nzrp + q) - ea, hi = __ldg(a.nzrp + q + 1) - ea;
                 V2 p{};
                 typename T::Norm2 ir{};
@@ -330,7 +338,7 @@ __global__ void __launch_bounds__(1024, 1) sart_persistent_kernel(SartArgs<T> a)
                 Acc b1 = 0, b2 = 0;
                 int j = -1;
                 if (q < qb) {
-                    j = __ldg(a.nzc + q);
+                    j = kDirect ? q : __ldg(a.nzc + q);
                     const int lo = __ldg(a.nzcp + q) - ea, hi = __ldg(a.nzcp + q + 1) - ea;
                     if (staged) {
                         for (int e = lo + sub; e < hi; e += LPC) {
@@ -427,6 +435,8 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
     a.timeout_ns = (unsigned long long)(tms * 1e6);
     a.expected = (unsigned)grid + (o.inject_barrier_fault ? 1u : 0u);
     a.tile_entries = TE;
+    a.direct_rows = 0;
+    a.direct_cols = 0;
 
     if ((e = cudaMemsetAsync(s->ctl, 0, sizeof(LaunchCtl), st)) != cudaSuccess) return cuda_fail(e, "solve: memset");
     // A result the launch never writes (a timeout) reads back as iters = -1.
@@ -464,3 +474,183 @@ int run_solve(splitsart_system* s, const void* p12, void* f12, const splitsart_s
 }
 
 }  // namespace splitsart
+
+// ---------------------------------------------------------------------------
+// Allocation-free solve.
+//
+// Some callers cannot call cudaMalloc. Examples: a process that reserves all
+// of its device memory up front and forbids allocation afterwards, and a
+// plugin that runs inside a host application which owns the GPU's memory
+// budget. Such a caller cannot create a system with splitsart_fold_system,
+// because that allocates. It can still hand in a folded system that it
+// placed in its own buffers.
+//
+// This variant runs the same persistent kernel on a plain folded CSR/CSC
+// (no compacted lists). Its working memory lives in one file-scope
+// static __device__ array of fixed size:
+//   the launch control block, the result, the per-CTA norm partials, and
+//   u12 for at most kStaticMaxRows rows.
+// Every GPU that loads the library holds this array until the process exits.
+// ---------------------------------------------------------------------------
+namespace splitsart {
+namespace {
+
+constexpr int kStaticMaxRows = 65536;
+constexpr int kMaxDevices = 64;
+
+struct StaticScratch {
+    LaunchCtl ctl;  // cleared at every call
+    SolveResultDev result;
+    double partials[2 * kMaxCtas];
+    float2 u12[kStaticMaxRows];
+};
+
+static __device__ __align__(256) unsigned char g_static_scratch[sizeof(StaticScratch)];
+
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device. It is looked up
+// once per device, on the first call made with that device current.
+int static_scratch_address(StaticScratch** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "solve_static: cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(SPLITSART_ERR_ARG, "solve_static: device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "solve_static: cudaGetSymbolAddress");
+        g_static_addr[dev] = ptr;
+    }
+    *out = reinterpret_cast<StaticScratch*>(g_static_addr[dev]);
+    return SPLITSART_OK;
+}
+
+__global__ void static_result_kernel(const StaticScratch* sc, splitsart_solve_info* info) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (sc->ctl.err != 0) {
+        info->iters = -1;
+        info->status = sc->ctl.err;
+        info->rho = NAN;
+        info->rr = NAN;
+        info->pp = NAN;
+    } else {
+        info->iters = sc->result.iters;
+        info->status = sc->result.status;
+        info->rho = sc->result.rho;
+        info->rr = sc->result.rr;
+        info->pp = sc->result.pp;
+    }
+}
+
+template <int LPC>
+int launch_static(StaticScratch* sc, int Mh, int Nh, const int32_t* rp, const int32_t* col, const float2* val,
+                  const int32_t* cp, const int32_t* row, const float2* valT, const float2* invR, const float2* invC,
+                  const float2* p12, float2* f12, const splitsart_solve_opts& o, cudaStream_t st) {
+    auto kern = sart_persistent_kernel<TF32, LPC, true>;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "solve_static: cudaGetDevice");
+    int nsm = 0, coop = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop) return fail(SPLITSART_ERR_CUDA, "solve_static: device lacks cooperative launch");
+    const int threads = o.block_threads > 0 ? o.block_threads : 1024;
+    if (threads % 32 != 0 || threads > 1024 || threads < 64)
+        return fail(SPLITSART_ERR_ARG, "solve_static: block_threads must be a multiple of 32 in [64, 1024]");
+    const int TE = default_tile_entries<TF32>();
+    const size_t dyn = sizeof(float2) * (size_t)TE;
+    e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return cuda_fail(e, "solve_static: shared memory attribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, dyn);
+    if (e != cudaSuccess) return cuda_fail(e, "solve_static: occupancy");
+    if (o.ctas_per_sm > 0 && o.ctas_per_sm < per_sm) per_sm = o.ctas_per_sm;
+    int grid = nsm * per_sm;
+    if (grid > kMaxCtas) grid = kMaxCtas;
+    if (grid < 1) return fail(SPLITSART_ERR_CUDA, "solve_static: kernel does not fit on an SM");
+
+    SartArgs<TF32> a{};
+    a.nzrp = rp;
+    a.nzcp = cp;
+    a.col = col;
+    a.val = val;
+    a.row = row;
+    a.valT = valT;
+    a.invR = invR;
+    a.invC = invC;
+    a.p12 = p12;
+    a.f12 = f12;
+    a.u12 = sc->u12;
+    a.partials = sc->partials;
+    a.ctl = &sc->ctl;
+    a.result = &sc->result;
+    a.max_iters = o.max_iters;
+    a.check_every = o.check_every > 0 ? o.check_every : 1;
+    a.lambda = o.lambda;
+    a.tol = o.tol;
+    const double tms = o.timeout_ms > 0 ? o.timeout_ms : 2000.0;
+    a.timeout_ns = (unsigned long long)(tms * 1e6);
+    a.expected = (unsigned)grid + (o.inject_barrier_fault ? 1u : 0u);
+    a.tile_entries = TE;
+    a.direct_rows = Mh;
+    a.direct_cols = Nh;
+    // The array keeps the previous call's contents: the control block must start at zero.
+    if ((e = cudaMemsetAsync(&sc->ctl, 0, sizeof(LaunchCtl), st)) != cudaSuccess)
+        return cuda_fail(e, "solve_static: clear control block");
+    void* args[] = {&a};
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(threads), args, dyn, st);
+    if (e != cudaSuccess) return cuda_fail(e, "solve_static: cooperative launch");
+    return SPLITSART_OK;
+}
+
+}  // namespace
+
+}  // namespace splitsart
+
+extern "C" int splitsart_solve_static(int64_t Mh, int64_t Nh, const int32_t* rp_dev, const int32_t* col_dev,
+                                      const void* val_dev, const int32_t* cp_dev, const int32_t* row_dev,
+                                      const void* valT_dev, const void* invR_dev, const void* invC_dev,
+                                      const void* p12_dev, void* f12_dev, const splitsart_solve_opts* opts,
+                                      splitsart_solve_info* info_dev, void* stream) {
+    using namespace splitsart;
+    if (!opts || !info_dev || !rp_dev || !cp_dev || !p12_dev || !f12_dev || !invR_dev || !invC_dev)
+        return fail(SPLITSART_ERR_ARG, "solve_static: NULL argument");
+    if (Mh <= 0 || Nh <= 0) return fail(SPLITSART_ERR_ARG, "solve_static: Mh and Nh must be positive");
+    if (Mh > kStaticMaxRows)
+        return fail(SPLITSART_ERR_ARG,
+                    "solve_static: Mh = %lld rows exceeds the static scratch capacity of %d rows; use splitsart_solve",
+                    (long long)Mh, kStaticMaxRows);
+    if (Nh > INT32_MAX) return fail(SPLITSART_ERR_ARG, "solve_static: Nh exceeds int32");
+    if (opts->max_iters < 0) return fail(SPLITSART_ERR_ARG, "solve_static: max_iters must be >= 0");
+    if (!(opts->lambda > 0.0) || !std::isfinite(opts->lambda))
+        return fail(SPLITSART_ERR_ARG, "solve_static: lambda must be > 0");
+    if (!(opts->tol >= 0.0)) return fail(SPLITSART_ERR_ARG, "solve_static: tol must be >= 0");
+    if (opts->check_every < 0 || !(opts->timeout_ms >= 0.0))
+        return fail(SPLITSART_ERR_ARG, "solve_static: bad check_every or timeout_ms");
+    StaticScratch* sc = nullptr;
+    int rc = static_scratch_address(&sc);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const auto* val = (const float2*)val_dev;
+    const auto* valT = (const float2*)valT_dev;
+    const auto* iR = (const float2*)invR_dev;
+    const auto* iC = (const float2*)invC_dev;
+    const auto* p12 = (const float2*)p12_dev;
+    auto* f12 = (float2*)f12_dev;
+    switch (opts->lanes_per_col > 0 ? opts->lanes_per_col : 8) {
+        case 1: rc = launch_static<1>(sc, (int)Mh, (int)Nh, rp_dev, col_dev, val, cp_dev, row_dev, valT, iR, iC, p12, f12, *opts, st); break;
+        case 2: rc = launch_static<2>(sc, (int)Mh, (int)Nh, rp_dev, col_dev, val, cp_dev, row_dev, valT, iR, iC, p12, f12, *opts, st); break;
+        case 4: rc = launch_static<4>(sc, (int)Mh, (int)Nh, rp_dev, col_dev, val, cp_dev, row_dev, valT, iR, iC, p12, f12, *opts, st); break;
+        case 8: rc = launch_static<8>(sc, (int)Mh, (int)Nh, rp_dev, col_dev, val, cp_dev, row_dev, valT, iR, iC, p12, f12, *opts, st); break;
+        case 16: rc = launch_static<16>(sc, (int)Mh, (int)Nh, rp_dev, col_dev, val, cp_dev, row_dev, valT, iR, iC, p12, f12, *opts, st); break;
+        case 32: rc = launch_static<32>(sc, (int)Mh, (int)Nh, rp_dev, col_dev, val, cp_dev, row_dev, valT, iR, iC, p12, f12, *opts, st); break;
+        default: return fail(SPLITSART_ERR_ARG, "solve_static: lanes_per_col must be 1, 2, 4, 8, 16 or 32");
+    }
+    if (rc) return rc;
+    static_result_kernel<<<1, 32, 0, st>>>(sc, info_dev);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SPLITSART_OK : cuda_fail(e, "solve_static: result launch");
+}

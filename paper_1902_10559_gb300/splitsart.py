@@ -79,6 +79,8 @@ _SIGS = {
     "splitsart_project": ([_P, _P, ctypes.c_int, _P, _P], ctypes.c_int),
     "splitsart_solve": ([_P, _P, _P, ctypes.POINTER(SolveOpts), _P], ctypes.c_int),
     "splitsart_solve_result": ([_P, ctypes.POINTER(SolveInfo)], ctypes.c_int),
+    "splitsart_solve_static": ([ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                ctypes.POINTER(SolveOpts), _P, _P], ctypes.c_int),
     "splitsart_last_error": ([ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
     "splitsart_version": ([], ctypes.c_char_p),
 }
@@ -289,6 +291,34 @@ def solve_result(system: System, raise_on_error: bool = True) -> dict:
     if rc != OK and raise_on_error:
         raise SplitSartError(rc, last_error())
     return {"iters": info.iters, "status": info.status, "rho": info.rho, "rr": info.rr, "pp": info.pp}
+
+
+def solve_static(Mh: int, Nh: int, rp, col, val, cp, row, valT, invR, invC, p12, f12, opts: SolveOpts, info,
+                 stream=None) -> None:
+    """Allocation-free solve on caller-owned buffers (see splitsart_solve_static in the header).
+
+    All arrays are CUDA tensors: rp/cp int32, col/row int32, and val/valT/invR/
+    invC/p12/f12 float32 pairs shaped [n, 2]. ``info`` is a CUDA uint8 tensor of
+    at least ``ctypes.sizeof(SolveInfo)`` bytes. Use ``read_info`` to decode it.
+    """
+    import torch
+    S = col.numel()
+    i32, f32 = torch.int32, torch.float32
+    if info.dtype != torch.uint8 or info.numel() < ctypes.sizeof(SolveInfo) or not info.is_cuda:
+        raise ValueError("info: expected a CUDA uint8 tensor of sizeof(SolveInfo) bytes")
+    _check(lib().splitsart_solve_static(
+        Mh, Nh, _dev_ptr(rp, Mh + 1, i32, "rp"), _dev_ptr(col, S, i32, "col"), _dev_ptr(val, 2 * S, f32, "val"),
+        _dev_ptr(cp, Nh + 1, i32, "cp"), _dev_ptr(row, S, i32, "row"), _dev_ptr(valT, 2 * S, f32, "valT"),
+        _dev_ptr(invR, 2 * Mh, f32, "invR"), _dev_ptr(invC, 2 * Nh, f32, "invC"),
+        _dev_ptr(p12, 2 * Mh, f32, "p12"), _dev_ptr(f12, 2 * Nh, f32, "f12"), ctypes.byref(opts), info.data_ptr(),
+        _stream_ptr(stream)))
+
+
+def read_info(info) -> dict:
+    """Decode a device splitsart_solve_info written by solve_static."""
+    raw = bytes(info[: ctypes.sizeof(SolveInfo)].cpu().numpy().tobytes())
+    s = SolveInfo.from_buffer_copy(raw)
+    return {"iters": s.iters, "status": s.status, "rho": s.rho, "rr": s.rr, "pp": s.pp}
 
 
 def version() -> str:
