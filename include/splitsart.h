@@ -233,14 +233,14 @@ int splitsart_project(splitsart_system* sys, const void* f_dev, int layout, void
  * Options of splitsart_solve. Zero-initialise the struct, then set fields.
  */
 typedef struct splitsart_solve_opts {
-    int32_t max_iters;     /* iteration cap, >= 0 */
+    int32_t max_iters;     /* iteration cap, in [0, 500000] */
     double lambda;         /* relaxation, 0 < lambda < 2 */
     double tol;            /* stop at the first k with rho_k <= tol; 0 = run max_iters */
     int32_t check_every;   /* test rho every this many iterations (>= 1; 0 means 1) */
     int32_t block_threads; /* threads per CTA, 0 = library default (256) */
     int32_t ctas_per_sm;   /* 0 = as many as fit */
     int32_t lanes_per_col; /* back-projection lanes per column, 0 = default (8); 1,2,4,8,16,32 */
-    int32_t reserved0;
+    int32_t kernel;        /* 0 = choose, 1 = stream the matrix from memory, 2 = keep it in shared memory */
     double timeout_ms;     /* limit of each grid-barrier wait; 0 = default (2000 ms) */
     int32_t inject_barrier_fault; /* test hook: the barrier also waits for a CTA that never comes */
     int32_t reserved1;

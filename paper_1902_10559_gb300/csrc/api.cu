@@ -90,6 +90,19 @@ int64_t read_S(splitsart_system* s) {
 
 }  // namespace
 
+int system_host_stats(splitsart_system* s, FoldStats* out) {
+    if (!s->have_stats) {
+        cudaError_t e = cudaStreamSynchronize(s->last);
+        if (e != cudaSuccess) return cuda_fail(e, "sync");
+        e = cudaMemcpy(&s->hstats, s->stats, sizeof(FoldStats), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "read fold stats");
+        if (s->Mh == 0) s->hstats = FoldStats{};
+        s->have_stats = true;
+    }
+    *out = s->hstats;
+    return SPLITSART_OK;
+}
+
 int fail(int code, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -339,7 +352,9 @@ extern "C" int splitsart_solve(splitsart_system* s, const void* p12, void* f12, 
                                void* stream) {
     if (!s || !o) return fail(SPLITSART_ERR_ARG, "solve: NULL argument");
     if ((s->Mh > 0 && !p12) || (s->Nh > 0 && !f12)) return fail(SPLITSART_ERR_ARG, "solve: NULL vector");
-    if (o->max_iters < 0) return fail(SPLITSART_ERR_ARG, "solve: max_iters must be >= 0");
+    if (o->max_iters < 0 || o->max_iters > 500000)
+        return fail(SPLITSART_ERR_ARG, "solve: max_iters must be in [0, 500000]");
+    if (o->kernel < 0 || o->kernel > 2) return fail(SPLITSART_ERR_ARG, "solve: kernel must be 0, 1 or 2");
     if (!(o->lambda > 0.0) || !std::isfinite(o->lambda)) return fail(SPLITSART_ERR_ARG, "solve: lambda must be > 0");
     if (!(o->tol >= 0.0)) return fail(SPLITSART_ERR_ARG, "solve: tol must be >= 0");
     if (o->check_every < 0) return fail(SPLITSART_ERR_ARG, "solve: check_every must be >= 0");

@@ -117,85 +117,66 @@ struct LaunchCtl {
     unsigned bar_gen;
     int err;       // 0, or a SPLITSART_ERR_* code
     int err_where; // barrier index at which a wait ran out
-    double sum0;   // grid totals published by the last CTA to arrive at a reducing barrier
-    double sum1;
 };
 
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).
-// - Thread 0 of each CTA arrives on a counter. The last arriver resets the
-//   counter and advances the generation.
-// - If `partials` is non-null, the last CTA first sums the per-CTA pairs
-//   partials[2b], partials[2b+1], b < gridDim.x, in a fixed order, and
-//   publishes the totals in ctl->sum0 and ctl->sum1. Every CTA reads them
-//   after the barrier. Every CTA obtains bitwise the same totals without
-//   reading all the partials itself.
-// - The other CTAs spin on the generation with a wall-clock limit and a spin
-//   cap. If either runs out, the wait records SPLITSART_ERR_TIMEOUT in
-//   ctl->err and stops waiting.
-// - `expected` is normally gridDim.x. A test passes gridDim.x + 1 to make the
-//   wait run out on purpose.
+// ctl->bar_count only ever grows during a launch:
+// - thread 0 of each CTA adds 1 with a release reduction (a posted write that
+//   needs no round trip);
+// - it then waits until the count reaches `target`, which is
+//   expected x (barrier index + 1).
+// The wait has a wall-clock limit and a spin cap. If either runs out, the wait
+// records SPLITSART_ERR_TIMEOUT in ctl->err and stops waiting. `expected` is
+// normally gridDim.x; a test passes gridDim.x + 1 to make the wait run out on
+// purpose.
 // Returns false, for every thread of the CTA, if any CTA has recorded an
 // error. The caller must then return.
-__device__ __forceinline__ bool grid_barrier(LaunchCtl* ctl, unsigned expected, unsigned long long timeout_ns,
-                                             int where, const double* partials = nullptr) {
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ bool grid_sync(LaunchCtl* ctl, unsigned target, unsigned long long timeout_ns, int where) {
     __shared__ int s_ok;
-    __shared__ int s_last;
-    __shared__ unsigned s_gen;
     __syncthreads();
     if (threadIdx.x == 0) {
-        s_gen = ld_acquire_gpu(&ctl->bar_gen);
-        __threadfence();
-        const unsigned prev = atomicAdd(&ctl->bar_count, 1u);
-        s_last = (prev == expected - 1);
-        if (s_last) __threadfence();
-    }
-    __syncthreads();
-    if (s_last) {
-        if (partials != nullptr && threadIdx.x < 32) {
-            const int lane = threadIdx.x;
-            double t0 = 0.0, t1 = 0.0;
-#pragma unroll 4
-            for (int b = lane; b < (int)gridDim.x; b += 32) {
-                t0 += __ldcg(partials + 2 * b);
-                t1 += __ldcg(partials + 2 * b + 1);
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                t0 += __shfl_xor_sync(0xffffffffu, t0, o);
-                t1 += __shfl_xor_sync(0xffffffffu, t1, o);
-            }
-            if (lane == 0) {
-                __stcg(&ctl->sum0, t0);
-                __stcg(&ctl->sum1, t1);
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            atomicExch(&ctl->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-            s_ok = ld_volatile(&ctl->err) == 0;
-        }
-    } else if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned gen = s_gen;
-        const unsigned long long t0 = global_ns();
-        const unsigned long long max_spins = timeout_ns / 32ull + (1ull << 20);
-        unsigned long long spins = 0;
-        while (ld_acquire_gpu(&ctl->bar_gen) == gen) {
-            if (ld_volatile(&ctl->err) != 0) { ok = 0; break; }
-            if (global_ns() - t0 > timeout_ns || ++spins > max_spins) {
-                if (atomicCAS(&ctl->err, 0, SPLITSART_ERR_TIMEOUT) == 0) ctl->err_where = where;
-                ok = 0;
-                break;
-            }
-            __nanosleep(32);
-        }
         __threadfence();
+        red_release_add(&ctl->bar_count, 1u);
+        if (ld_acquire_gpu(&ctl->bar_count) < target) {
+            const unsigned long long t0 = global_ns();
+            const unsigned long long max_spins = timeout_ns / 32ull + (1ull << 20);
+            unsigned long long spins = 0;
+            while (ld_acquire_gpu(&ctl->bar_count) < target) {
+                if (ld_volatile(&ctl->err) != 0) { ok = 0; break; }
+                if (global_ns() - t0 > timeout_ns || ++spins > max_spins) {
+                    if (atomicCAS(&ctl->err, 0, SPLITSART_ERR_TIMEOUT) == 0) ctl->err_where = where;
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(20);
+            }
+        }
         if (ld_volatile(&ctl->err) != 0) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// Warp 0: sum the per-CTA pairs partials[2b], partials[2b+1] (b < nparts) in
+// a fixed order. Every CTA obtains bitwise the same totals.
+__device__ __forceinline__ void grid_totals(const double* partials, int nparts, int lane, double& t0, double& t1) {
+    t0 = 0.0;
+    t1 = 0.0;
+#pragma unroll 4
+    for (int b = lane; b < nparts; b += 32) {
+        t0 += __ldcg(partials + 2 * b);
+        t1 += __ldcg(partials + 2 * b + 1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+        t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+    }
 }
 
 }  // namespace splitsart

@@ -224,6 +224,7 @@ __global__ void fold_fill_kernel(int64_t Mh, int N, const int64_t* __restrict__ 
     using NS = decltype(N2{}.x);
     invR[i] = N2{(NS)(R1 > 0.0 ? 1.0 / R1 : 0.0), (NS)(R2 > 0.0 ? 1.0 / R2 : 0.0)};
     if (out == frp[i]) atomicAdd(reinterpret_cast<unsigned long long*>(&stats->empty_rows), 1ULL);
+    else atomicMax(&stats->max_row, out - frp[i]);
     if (zeros) atomicAdd(reinterpret_cast<unsigned long long*>(&stats->exact_zeros), (unsigned long long)zeros);
     if (i == Mh - 1) stats->S = frp[Mh];
 }
@@ -255,7 +256,8 @@ __global__ void csc_place_kernel(int64_t Mh, const int32_t* __restrict__ frp, co
 template <class T>
 __global__ void csc_sort_colsum_kernel(int64_t Nh, const int32_t* __restrict__ cp, int32_t* __restrict__ row,
                                        typename T::Pair* __restrict__ valT, const float2* __restrict__ scale,
-                                       double2* __restrict__ Csum, typename T::Norm2* __restrict__ invC) {
+                                       double2* __restrict__ Csum, typename T::Norm2* __restrict__ invC,
+                                       FoldStats* __restrict__ stats) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= Nh) return;
     const int32_t b = cp[j], e = cp[j + 1];
@@ -285,6 +287,7 @@ __global__ void csc_sort_colsum_kernel(int64_t Nh, const int32_t* __restrict__ c
         C2 += fabs(d2);
     }
     Csum[j] = make_double2(C1, C2);
+    if (e > b) atomicMax(&stats->max_col, e - b);
     using N2 = typename T::Norm2;
     using NS = decltype(N2{}.x);
     invC[j] = N2{(NS)(C1 > 0.0 ? 1.0 / C1 : 0.0), (NS)(C2 > 0.0 ? 1.0 / C2 : 0.0)};
@@ -361,7 +364,7 @@ int fold_typed(splitsart_system* s, cudaStream_t st) {
                                                                           s->cp, s->cnt, s->row, (Pair*)s->valT);
     if (Nh > 0)
         csc_sort_colsum_kernel<T><<<(unsigned)((Nh + 127) / 128), 128, 0, st>>>(
-            Nh, s->cp, s->row, (Pair*)s->valT, s->scale, s->Csum, (N2*)s->invC);
+            Nh, s->cp, s->row, (Pair*)s->valT, s->scale, s->Csum, (N2*)s->invC, s->stats);
     rc = compact(s->cp, Nh, s->flags, s->cnt, s->scan_tmp, s->nzc, s->nzcp, nullptr, &s->stats->n_nzc, nullptr, st);
     if (rc) return rc;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "fold launch");

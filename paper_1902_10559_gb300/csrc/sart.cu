@@ -124,7 +124,7 @@ __device__ int plan_tiles(const int32_t* ptr, int n, int TE, int* tiles, int lan
 // kDirect: the caller's plain folded CSR/CSC is used as is (no compacted
 // lists). Empty rows then pass through the row loop with no entries.
 template <class T, int LPC, bool kDirect = false>
-__global__ void __launch_bounds__(1024, 1) sart_persistent_kernel(SartArgs<T> a) {
+__global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
     using Acc = typename T::Acc;
     using V2 = typename T::Vec2;
     using Pair = typename T::Pair;
@@ -179,8 +179,8 @@ __global__ void __launch_bounds__(1024, 1) sart_persistent_kernel(SartArgs<T> a)
             ppz = t;  // meaningful in thread 0 only
         }
     }
-    int barrier_no = 0;
-    if (!grid_barrier(a.ctl, a.expected, a.timeout_ns, barrier_no++)) return;
+    unsigned nbar = 0;
+    if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     const int nrt = s_nrt, nct = s_nct;
 
     for (int k = 0;; ++k) {
@@ -282,12 +282,21 @@ __global__ void __launch_bounds__(1024, 1) sart_persistent_kernel(SartArgs<T> a)
             __stcg(a.partials + 2 * blockIdx.x, t0);
             __stcg(a.partials + 2 * blockIdx.x + 1, t1);
         }
-        if (!grid_barrier(a.ctl, a.expected, a.timeout_ns, barrier_no++, a.partials)) return;
+        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
 
-        // ---- stop test on the published totals ----
+        // ---- stop test: every CTA sums the partials in the same order ----
         const bool last = (k >= a.max_iters);
         if (last || (k % a.check_every == 0)) {
-            const double trr = __ldcg(&a.ctl->sum0), tpp = __ldcg(&a.ctl->sum1);
+            if (wib == 0) {
+                double t0, t1;
+                grid_totals(a.partials, gridDim.x, lane, t0, t1);
+                if (lane == 0) {
+                    s_red[0][0] = t0;
+                    s_red[1][0] = t1;
+                }
+            }
+            __syncthreads();
+            const double trr = s_red[0][0], tpp = s_red[1][0];
             const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
             if (last || rho <= a.tol) {
                 if (blockIdx.x == 0 && tid == 0) {
@@ -373,7 +382,319 @@ __global__ void __launch_bounds__(1024, 1) sart_persistent_kernel(SartArgs<T> a)
             }
             __syncthreads();
         }
-        if (!grid_barrier(a.ctl, a.expected, a.timeout_ns, barrier_no++)) return;
+        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory-resident variant, for systems whose per-CTA share fits on chip.
+//
+// Each CTA copies its part of the folded matrix into shared memory once per
+// launch:
+// - a contiguous range of non-empty rows, and one of non-empty columns,
+//   balanced by their shared-memory bytes;
+// - values, 16-bit indices, and the per-row/column metadata (p, 1/R, 1/C,
+//   its own f).
+// After that, an iteration's global traffic is only the gathers of f (forward)
+// and of u (back), the stores of u and f, and the norm partials. Each row and
+// column is summed in the streaming kernel's lane order. The products are
+// fused into FMAs here, so the last bits can differ from that kernel.
+// ---------------------------------------------------------------------------
+
+// Shared-memory bytes per entry and per row/column of the resident layout.
+template <class T>
+struct ResidentBytes {
+    static constexpr int kEntry = (int)sizeof(typename T::Pair) + 2;
+    static constexpr int kRow = 4 + 4 + (int)sizeof(typename T::Vec2) + (int)sizeof(typename T::Norm2) +
+                                (T::kQuant ? (int)sizeof(float2) : 0);
+    static constexpr int kCol = 4 + 4 + (int)sizeof(typename T::Norm2) + (int)sizeof(typename T::Vec2);
+    static constexpr int kSlack = 12 * 16 + 16;  // alignment of 12 segments, plus the end pointers
+};
+
+// First q in [lo, hi] with WE*ptr[q] + WR*q >= t (a non-decreasing key).
+__device__ __forceinline__ int warp_lower_bound_w(const int32_t* ptr, int lo, int hi, long long t, int WE, int WR,
+                                                  int lane) {
+    while (hi - lo > 32) {
+        const int step = (hi - lo + 31) / 32;
+        const int idx = lo + lane * step;
+        const bool below = idx < hi && (long long)WE * __ldg(ptr + idx) + (long long)WR * idx < t;
+        const int c = __popc(__ballot_sync(0xffffffffu, below));
+        if (c == 0) return lo;
+        const int nlo = lo + (c - 1) * step + 1;
+        hi = min(lo + c * step, hi);
+        lo = nlo;
+    }
+    const int idx = lo + lane;
+    const bool below = idx < hi && (long long)WE * __ldg(ptr + idx) + (long long)WR * idx < t;
+    return lo + __popc(__ballot_sync(0xffffffffu, below));
+}
+
+// One warp: this CTA's range [q0, q1) of [0, n), balanced by WE*entries + WR*items.
+__device__ __forceinline__ int2 resident_range(const int32_t* ptr, int n, int WE, int WR, int lane) {
+    const long long total = (long long)WE * __ldg(ptr + n) + (long long)WR * n;
+    const long long G = gridDim.x, b = blockIdx.x;
+    const int q0 = warp_lower_bound_w(ptr, 0, n, total * b / G, WE, WR, lane);
+    const int q1 = (b == G - 1) ? n : warp_lower_bound_w(ptr, 0, n, total * (b + 1) / G, WE, WR, lane);
+    return make_int2(q0, q1);
+}
+
+__device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+constexpr int kResUnroll = 4;
+
+template <class T, int LPC>
+__global__ void __launch_bounds__(1024, 1) sart_resident_kernel(SartArgs<T> a, int smem_bytes) {
+    using Acc = typename T::Acc;
+    using V2 = typename T::Vec2;
+    using N2 = typename T::Norm2;
+    using Pair = typename T::Pair;
+    using B = ResidentBytes<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int2 s_rows, s_cols;
+    __shared__ double s_red[2][32];
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int wib = tid >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int BD = blockDim.x;
+    constexpr int kGroupsPerWarp = 32 / LPC;
+    const int sub = lane % LPC;
+    const Acc lam = (Acc)a.lambda;
+
+    // ---- launch prologue: ranges, shared-memory layout, and the copy-in ----
+    const int n_nzr = a.stats->n_nzr, n_nzc = a.stats->n_nzc, n_zr = a.stats->n_zr;
+    if (wib == 0) {
+        const int2 r = resident_range(a.nzrp, n_nzr, B::kEntry, B::kRow, lane);
+        if (lane == 0) s_rows = r;
+    } else if (wib == 1) {
+        const int2 r = resident_range(a.nzcp, n_nzc, B::kEntry, B::kCol, lane);
+        if (lane == 0) s_cols = r;
+    }
+    __syncthreads();
+    const int q0 = s_rows.x, nr = s_rows.y - s_rows.x;
+    const int c0 = s_cols.x, nc = s_cols.y - s_cols.x;
+    const int fea = __ldg(a.nzrp + q0), nfe = __ldg(a.nzrp + q0 + nr) - fea;
+    const int bea = __ldg(a.nzcp + c0), nbe = __ldg(a.nzcp + c0 + nc) - bea;
+
+    size_t off = 0;
+    Pair* f_val = reinterpret_cast<Pair*>(smem_raw + off);
+    off = align16(off + sizeof(Pair) * nfe);
+    uint16_t* f_idx = reinterpret_cast<uint16_t*>(smem_raw + off);
+    off = align16(off + 2 * (size_t)nfe);
+    int* r_ptr = reinterpret_cast<int*>(smem_raw + off);
+    off = align16(off + 4 * (size_t)(nr + 1));
+    int* r_id = reinterpret_cast<int*>(smem_raw + off);
+    off = align16(off + 4 * (size_t)nr);
+    V2* r_p = reinterpret_cast<V2*>(smem_raw + off);
+    off = align16(off + sizeof(V2) * nr);
+    N2* r_ir = reinterpret_cast<N2*>(smem_raw + off);
+    off = align16(off + sizeof(N2) * nr);
+    float2* r_sc = reinterpret_cast<float2*>(smem_raw + off);
+    off = align16(off + (T::kQuant ? sizeof(float2) * nr : 0));
+    Pair* b_val = reinterpret_cast<Pair*>(smem_raw + off);
+    off = align16(off + sizeof(Pair) * nbe);
+    uint16_t* b_idx = reinterpret_cast<uint16_t*>(smem_raw + off);
+    off = align16(off + 2 * (size_t)nbe);
+    int* c_ptr = reinterpret_cast<int*>(smem_raw + off);
+    off = align16(off + 4 * (size_t)(nc + 1));
+    int* c_id = reinterpret_cast<int*>(smem_raw + off);
+    off = align16(off + 4 * (size_t)nc);
+    N2* c_ic = reinterpret_cast<N2*>(smem_raw + off);
+    off = align16(off + sizeof(N2) * nc);
+    V2* c_f = reinterpret_cast<V2*>(smem_raw + off);
+    off = align16(off + sizeof(V2) * nc);
+
+    const bool fits = off <= (size_t)smem_bytes;
+    if (!fits) {
+        if (tid == 0) atomicCAS(&a.ctl->err, 0, SPLITSART_ERR_ARG);
+    } else {
+        for (int e = tid; e < nfe; e += BD) {
+            f_val[e] = ldg(a.val + fea + e);
+            f_idx[e] = (uint16_t)__ldg(a.col + fea + e);
+        }
+        for (int q = tid; q < nr; q += BD) {
+            const int i = __ldg(a.nzr + q0 + q);
+            r_ptr[q] = __ldg(a.nzrp + q0 + q) - fea;
+            r_id[q] = i;
+            r_p[q] = ldg(a.p12 + i);
+            r_ir[q] = ldg(a.invR + i);
+            if constexpr (T::kQuant) r_sc[q] = ldg(a.scale + i);
+        }
+        if (tid == 0) r_ptr[nr] = nfe;
+        for (int e = tid; e < nbe; e += BD) {
+            b_val[e] = ldg(a.valT + bea + e);
+            b_idx[e] = (uint16_t)__ldg(a.row + bea + e);
+        }
+        for (int q = tid; q < nc; q += BD) {
+            const int j = __ldg(a.nzc + c0 + q);
+            c_ptr[q] = __ldg(a.nzcp + c0 + q) - bea;
+            c_id[q] = j;
+            c_ic[q] = ldg(a.invC + j);
+            c_f[q] = ldcg(a.f12 + j);
+        }
+        if (tid == 0) c_ptr[nc] = nbe;
+    }
+    double ppz = 0.0;  // this CTA's share of sum(p1^2 + p2^2) over the empty rows
+    {
+        const long long G = gridDim.x, b = blockIdx.x;
+        const int z0 = (int)(n_zr * b / G), z1 = (int)(n_zr * (b + 1) / G);
+        for (int z = z0 + tid; z < z1; z += BD) {
+            const V2 p = ldg(a.p12 + __ldg(a.zr + z));
+            ppz += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+        }
+        ppz = warp_sum(ppz);
+        if (lane == 0) s_red[0][wib] = ppz;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < nwarps; ++w) t += s_red[0][w];
+            ppz = t;  // meaningful in thread 0 only
+        }
+    }
+    unsigned nbar = 0;
+    if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+
+    for (int k = 0;; ++k) {
+        // ---- forward: r = p - A f, u = r / R, and the norm partials ----
+        double rr = 0.0, pp = 0.0;
+        for (int q = wib; q < nr; q += nwarps) {
+            const int lo = r_ptr[q], hi = r_ptr[q + 1];
+            Acc s1 = 0, s2 = 0;
+            for (int base = lo; base < hi; base += 32 * kResUnroll) {
+                V2 fv[kResUnroll];
+                Pair v[kResUnroll];
+#pragma unroll
+                for (int u = 0; u < kResUnroll; ++u) {
+                    const int e = base + u * 32 + lane;
+                    if (e < hi) {
+                        v[u] = f_val[e];
+                        fv[u] = ldcg(a.f12 + f_idx[e]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kResUnroll; ++u) {
+                    const int e = base + u * 32 + lane;
+                    if (e < hi) {
+                        Acc a1, a2;
+                        T::decode(v[u], a1, a2);
+                        s1 += a1 * fv[u].x;
+                        s2 += a2 * fv[u].y;
+                    }
+                }
+            }
+            s1 = warp_sum(s1);
+            s2 = warp_sum(s2);
+            if (lane == 0) {
+                const V2 p = r_p[q];
+                const N2 ir = r_ir[q];
+                V2 u;
+                if constexpr (T::kQuant) {
+                    const float2 sc = r_sc[q];
+                    s1 *= sc.x;
+                    s2 *= sc.y;
+                    const Acc r1 = p.x - s1, r2 = p.y - s2;
+                    u.x = (Acc)((double)r1 * ir.x * (double)sc.x);
+                    u.y = (Acc)((double)r2 * ir.y * (double)sc.y);
+                    rr += (double)r1 * (double)r1 + (double)r2 * (double)r2;
+                } else {
+                    const Acc r1 = p.x - s1, r2 = p.y - s2;
+                    u.x = r1 * ir.x;
+                    u.y = r2 * ir.y;
+                    rr += (double)r1 * (double)r1 + (double)r2 * (double)r2;
+                }
+                stcg(a.u12 + r_id[q], u);
+                pp += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+            }
+        }
+        if (lane == 0) {
+            s_red[0][wib] = rr;
+            s_red[1][wib] = pp;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double t0 = ppz, t1 = ppz;  // an empty row's residual is its p
+            for (int w = 0; w < nwarps; ++w) {
+                t0 += s_red[0][w];
+                t1 += s_red[1][w];
+            }
+            __stcg(a.partials + 2 * blockIdx.x, t0);
+            __stcg(a.partials + 2 * blockIdx.x + 1, t1);
+        }
+        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+
+        // ---- stop test: every CTA sums the partials in the same order ----
+        const bool last = (k >= a.max_iters);
+        if (last || (k % a.check_every == 0)) {
+            if (wib == 0) {
+                double t0, t1;
+                grid_totals(a.partials, gridDim.x, lane, t0, t1);
+                if (lane == 0) {
+                    s_red[0][0] = t0;
+                    s_red[1][0] = t1;
+                }
+            }
+            __syncthreads();
+            const double trr = s_red[0][0], tpp = s_red[1][0];
+            const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
+            if (last || rho <= a.tol) {
+                if (blockIdx.x == 0 && tid == 0) {
+                    a.result->iters = k;
+                    a.result->status = SPLITSART_OK;
+                    a.result->rho = rho;
+                    a.result->rr = trr;
+                    a.result->pp = tpp;
+                }
+                return;
+            }
+        }
+
+        // ---- back-projection and update: f += lambda (A^T u) / C ----
+        for (int g0 = wib * kGroupsPerWarp; g0 < nc; g0 += nwarps * kGroupsPerWarp) {
+            const int q = g0 + lane / LPC;
+            Acc b1 = 0, b2 = 0;
+            if (q < nc) {
+                const int lo = c_ptr[q], hi = c_ptr[q + 1];
+                for (int base = lo + sub; base < hi; base += LPC * kResUnroll) {
+                    V2 uv[kResUnroll];
+                    Pair v[kResUnroll];
+#pragma unroll
+                    for (int u = 0; u < kResUnroll; ++u) {
+                        const int e = base + u * LPC;
+                        if (e < hi) {
+                            v[u] = b_val[e];
+                            uv[u] = ldcg(a.u12 + b_idx[e]);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kResUnroll; ++u) {
+                        const int e = base + u * LPC;
+                        if (e < hi) {
+                            Acc a1, a2;
+                            T::decode(v[u], a1, a2);
+                            b1 += a1 * uv[u].x;
+                            b2 += a2 * uv[u].y;
+                        }
+                    }
+                }
+            }
+            b1 = warp_sum(b1, LPC);
+            b2 = warp_sum(b2, LPC);
+            if (sub == 0 && q < nc) {
+                const N2 ic = c_ic[q];
+                V2 f = c_f[q];
+                if constexpr (T::kQuant) {
+                    f.x += (Acc)((double)(lam * b1) * ic.x);
+                    f.y += (Acc)((double)(lam * b2) * ic.y);
+                } else {
+                    f.x += lam * b1 * ic.x;
+                    f.y += lam * b2 * ic.y;
+                }
+                c_f[q] = f;
+                stcg(a.f12 + c_id[q], f);
+            }
+        }
+        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     }
 }
 
@@ -382,32 +703,9 @@ constexpr int default_tile_entries() {
     return sizeof(typename T::Vec2) == 16 ? 8192 : 12288;
 }
 
-template <class T, int LPC>
-int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o, cudaStream_t st) {
-    auto kern = sart_persistent_kernel<T, LPC>;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "solve: cudaGetDevice");
-    int nsm = 0, coop = 0;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    if (!coop) return fail(SPLITSART_ERR_CUDA, "solve: device lacks cooperative launch");
-    const int threads = o.block_threads > 0 ? o.block_threads : 1024;
-    if (threads % 32 != 0 || threads > 1024 || threads < 64)
-        return fail(SPLITSART_ERR_ARG, "solve: block_threads must be a multiple of 32 in [64, 1024]");
-    const int TE = default_tile_entries<T>();
-    const size_t dyn = sizeof(typename T::Vec2) * (size_t)TE;
-    e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return cuda_fail(e, "solve: shared memory attribute");
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, dyn);
-    if (e != cudaSuccess) return cuda_fail(e, "solve: occupancy");
-    if (o.ctas_per_sm > 0 && o.ctas_per_sm < per_sm) per_sm = o.ctas_per_sm;
-    int grid = nsm * per_sm;
-    if (grid > kMaxCtas) grid = kMaxCtas;
-    if (grid < 1) return fail(SPLITSART_ERR_CUDA, "solve: kernel does not fit on an SM");
-
-    SartArgs<T> a;
+template <class T>
+void fill_args(SartArgs<T>& a, splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o,
+               unsigned grid) {
     a.nzr = s->nzr;
     a.nzrp = s->nzrp;
     a.zr = s->zr;
@@ -433,17 +731,86 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
     a.tol = o.tol;
     const double tms = o.timeout_ms > 0 ? o.timeout_ms : 2000.0;
     a.timeout_ns = (unsigned long long)(tms * 1e6);
-    a.expected = (unsigned)grid + (o.inject_barrier_fault ? 1u : 0u);
-    a.tile_entries = TE;
+    a.expected = grid + (o.inject_barrier_fault ? 1u : 0u);
+    a.tile_entries = default_tile_entries<T>();
     a.direct_rows = 0;
     a.direct_cols = 0;
+}
+
+// Upper bound of one CTA's resident shared-memory bytes for a grid of G CTAs.
+template <class T>
+long long resident_bound(const FoldStats& fs, long long G) {
+    using B = ResidentBytes<T>;
+    const long long Wr = (long long)B::kEntry * fs.S + (long long)B::kRow * fs.n_nzr;
+    const long long Wc = (long long)B::kEntry * fs.S + (long long)B::kCol * fs.n_nzc;
+    return (Wr + G - 1) / G + (long long)B::kEntry * fs.max_row + B::kRow + (Wc + G - 1) / G +
+           (long long)B::kEntry * fs.max_col + B::kCol + B::kSlack;
+}
+
+template <class T, int LPC>
+int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o, cudaStream_t st) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "solve: cudaGetDevice");
+    int nsm = 0, coop = 0, smem_optin = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!coop) return fail(SPLITSART_ERR_CUDA, "solve: device lacks cooperative launch");
+    const int threads = o.block_threads > 0 ? o.block_threads : 1024;
+    if (threads % 32 != 0 || threads > 1024 || threads < 64)
+        return fail(SPLITSART_ERR_ARG, "solve: block_threads must be a multiple of 32 in [64, 1024]");
+    FoldStats fs;
+    int rc = system_host_stats(s, &fs);
+    if (rc) return rc;
+
+    // Shared-memory residency: one CTA per SM, 16-bit indices.
+    auto rkern = sart_resident_kernel<T, LPC>;
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, (const void*)rkern);
+    if (e != cudaSuccess) return cuda_fail(e, "solve: kernel attributes");
+    const long long res_avail = (long long)smem_optin - (long long)fa.sharedSizeBytes;
+    const bool res_ok = s->Mh <= 65536 && s->Nh <= 65536 && resident_bound<T>(fs, nsm) <= res_avail;
+    if (o.kernel == 2 && !res_ok)
+        return fail(SPLITSART_ERR_ARG, "solve: the system does not fit in shared memory (need %lld of %lld bytes per SM)",
+                    resident_bound<T>(fs, nsm), res_avail);
+    const bool use_res = o.kernel == 2 || (o.kernel == 0 && res_ok);
+
+    SartArgs<T> a;
+    void* kern;
+    size_t dyn;
+    int grid;
+    int smem_bytes = 0;
+    if (use_res) {
+        kern = (void*)rkern;
+        dyn = (size_t)res_avail;
+        smem_bytes = (int)dyn;
+        grid = nsm;
+    } else {
+        kern = (void*)sart_stream_kernel<T, LPC>;
+        dyn = sizeof(typename T::Vec2) * (size_t)default_tile_entries<T>();
+    }
+    e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return cuda_fail(e, "solve: shared memory attribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, threads, dyn);
+    if (e != cudaSuccess) return cuda_fail(e, "solve: occupancy");
+    if (per_sm < 1) return fail(SPLITSART_ERR_CUDA, "solve: kernel does not fit on an SM");
+    if (!use_res) {
+        if (o.ctas_per_sm > 0 && o.ctas_per_sm < per_sm) per_sm = o.ctas_per_sm;
+        grid = nsm * per_sm;
+        if (grid > kMaxCtas) grid = kMaxCtas;
+    }
+    fill_args<T>(a, s, p12, f12, o, (unsigned)grid);
 
     if ((e = cudaMemsetAsync(s->ctl, 0, sizeof(LaunchCtl), st)) != cudaSuccess) return cuda_fail(e, "solve: memset");
     // A result the launch never writes (a timeout) reads back as iters = -1.
     if ((e = cudaMemsetAsync(s->result, 0xff, sizeof(SolveResultDev), st)) != cudaSuccess)
         return cuda_fail(e, "solve: memset");
-    void* args[] = {&a};
-    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(threads), args, dyn, st);
+    void* args_stream[] = {&a};
+    void* args_res[] = {&a, &smem_bytes};
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(threads), use_res ? args_res : args_stream,
+                                    dyn, st);
     if (e != cudaSuccess) return cuda_fail(e, "solve: cooperative launch");
     return SPLITSART_OK;
 }
@@ -549,7 +916,7 @@ template <int LPC>
 int launch_static(StaticScratch* sc, int Mh, int Nh, const int32_t* rp, const int32_t* col, const float2* val,
                   const int32_t* cp, const int32_t* row, const float2* valT, const float2* invR, const float2* invC,
                   const float2* p12, float2* f12, const splitsart_solve_opts& o, cudaStream_t st) {
-    auto kern = sart_persistent_kernel<TF32, LPC, true>;
+    auto kern = sart_stream_kernel<TF32, LPC, true>;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "solve_static: cudaGetDevice");

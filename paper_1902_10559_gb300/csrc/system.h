@@ -21,7 +21,9 @@ struct FoldStats {
     int n_nzr;              // rows with entries
     int n_nzc;              // columns with entries
     int n_zr;               // rows without entries
-    int pad2;
+    int max_row;            // longest folded row
+    int max_col;            // longest folded column
+    int pad3[3];
 };
 
 // Result of one solve, written by CTA 0 of the persistent launch.
@@ -43,6 +45,8 @@ struct splitsart_system {
     int64_t S = -1;  // host copy, read lazily
     int64_t device_bytes = 0;
     cudaStream_t last = nullptr;
+    bool have_stats = false;  // host copy of the fold statistics (identical across refolds)
+    splitsart::FoldStats hstats{};
 
     // Uploaded first-half rows of A (FP64).
     int64_t* hrp = nullptr;
@@ -95,4 +99,6 @@ int run_project(splitsart_system* s, const void* f, int layout, void* p, cudaStr
 // Defined in sart.cu.
 int run_solve(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o, cudaStream_t st);
 int cuda_fail(cudaError_t e, const char* what);
+// Defined in api.cu: the fold statistics on the host (one synchronisation on first use).
+int system_host_stats(splitsart_system* s, FoldStats* out);
 }  // namespace splitsart

@@ -291,3 +291,30 @@ def test_realistic_fp32_solve_matches_oracle(ss, realistic):
     assert info["iters"] == 200
     assert rel(f, osplit.recombine(ref["f1"], ref["f2"])) <= 1e-4
     assert abs(info["rho"] - ref["rho"]) <= 1e-4 * ref["rho"]
+
+
+@pytest.mark.parametrize("dt,tol", [("f64", 1e-10), ("f32", 1e-4), ("bf16", 1e-4)])
+def test_resident_and_streaming_kernels_agree_with_oracle(ss, tiny, dt, tol):
+    """Both solve kernels (matrix kept in shared memory; matrix streamed) reproduce the oracle on stored values."""
+    geom = ss.make_geometry(tiny.g)
+    sysm = ss.fold_system(geom, ss.DTYPE_NAMES[dt])
+    out = sysm.export()
+    Mh, Nh = tiny.g.M // 2, tiny.g.N // 2
+    H1 = sp.csr_matrix((out["a1"], out["col"], out["row_ptr"]), shape=(Mh, Nh))
+    H2 = sp.csr_matrix((out["a2"], out["col"], out["row_ptr"]), shape=(Mh, Nh))
+    ref = osart.split_sart(H1, H2, tiny.p1, tiny.p2, 1.0, 60)
+    f_ref = osplit.recombine(ref["f1"], ref["f2"])
+    for kernel in (1, 2):
+        info, f12, f = run_solve(ss, sysm, tiny.p, 60, 1.0, kernel=kernel)
+        assert info["iters"] == 60
+        assert rel(f, f_ref) <= tol, (kernel, rel(f, f_ref))
+        assert abs(info["rho"] - ref["rho"]) <= tol * ref["rho"]
+
+
+@pytest.mark.slow
+def test_realistic_kernels_agree(ss, realistic):
+    c = realistic
+    sysm = ss.fold_system(ss.make_geometry(c.g), ss.F32)
+    a = run_solve(ss, sysm, c.p, 50, 0.8, kernel=1)
+    b = run_solve(ss, sysm, c.p, 50, 0.8, kernel=2)
+    assert rel(a[2], b[2]) <= 1e-5 and abs(a[0]["rho"] - b[0]["rho"]) <= 1e-5 * b[0]["rho"]
