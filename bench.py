@@ -47,7 +47,7 @@ NOISE = 0.01
 CONFIG_ID = 2
 N_ELLIPSES = 20
 PROFILE = os.path.join(ROOT, "profiles", "sart_persistent_realistic_fp32.txt")
-KERNEL_SRC = os.path.join(ROOT, "paper_1902_10559_gb300", "csrc", "sart.cu")
+KERNEL_SRC = os.path.join(ROOT, "paper_1902_10559_gb300", "csrc", "sart.cu")  # solve kernels
 
 
 def workload_config(S=None):
@@ -292,7 +292,7 @@ def run_native(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": g.M * 4, "d2h_bytes_per_step": g.N * 4},
         "gpu_launches": n_launch["step"] * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "sart_persistent_kernel<TF32,8>",
+                     "traffic": traffic, "kernel": "sart_resident_kernel<TF32,8> (matrix slice kept in shared memory)",
                      "algorithmic_bytes_per_launch": alg, "peak_source": f"{peak_kind} hbm_gbs",
                      "note": "working set (~35 MB/iteration) is L2-resident within a solve"},
         "clocks": clocks.summary(),

@@ -84,8 +84,16 @@ __device__ __forceinline__ __half2 ldg(const __half2* p) {
     return *reinterpret_cast<__half2*>(&v);
 }
 
-// L2-coherent loads and stores (bypassing L1), for vectors that other CTAs of
-// the same persistent launch rewrite between grid barriers.
+// Loads and stores of the vectors that CTAs of one persistent launch rewrite
+// between grid barriers.
+// - Stores go to L2 (st.global.cg).
+// - Gathers may use L1 (ld.global.ca). Every such load follows the grid
+//   barrier's acquire and a CTA barrier, so under the PTX memory model it
+//   observes every write made before the barrier's release; no stale line
+//   can be read.
+// - ldcg reads L2 directly, for data read once.
+__device__ __forceinline__ float2 ldca(const float2* p) { return __ldca(p); }
+__device__ __forceinline__ double2 ldca(const double2* p) { return __ldca(p); }
 __device__ __forceinline__ float2 ldcg(const float2* p) { return __ldcg(p); }
 __device__ __forceinline__ double2 ldcg(const double2* p) { return __ldcg(p); }
 __device__ __forceinline__ void stcg(float2* p, float2 v) { __stcg(p, v); }
@@ -156,6 +164,7 @@ __device__ __forceinline__ bool grid_sync(LaunchCtl* ctl, unsigned target, unsig
                 __nanosleep(20);
             }
         }
+        __threadfence();  // acquire side: later loads of this CTA see the other CTAs' writes
         if (ld_volatile(&ctl->err) != 0) ok = 0;
         s_ok = ok;
     }

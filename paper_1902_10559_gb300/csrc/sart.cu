@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
                     for (int u = 0; u < kUnroll; ++u) {
                         const int e = base + u * BD + tid;
                         if (e < n) {
-                            const V2 fv = ldcg(a.f12 + c[u]);
+                            const V2 fv = ldca(a.f12 + c[u]);
                             Acc a1, a2;
                             T::decode(v[u], a1, a2);
                             prod[e] = V2{a1 * fv.x, a2 * fv.y};
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
                     for (int u = 0; u < kUnroll; ++u) {
                         const int e = base + u * BD + tid;
                         if (e < n) {
-                            const V2 uv = ldcg(a.u12 + r[u]);
+                            const V2 uv = ldca(a.u12 + r[u]);
                             Acc a1, a2;
                             T::decode(v[u], a1, a2);
                             prod[e] = V2{a1 * uv.x, a2 * uv.y};
@@ -396,9 +396,18 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
 // - values, 16-bit indices, and the per-row/column metadata (p, 1/R, 1/C,
 //   its own f).
 // After that, an iteration's global traffic is only the gathers of f (forward)
-// and of u (back), the stores of u and f, and the norm partials. Each row and
-// column is summed in the streaming kernel's lane order. The products are
-// fused into FMAs here, so the last bits can differ from that kernel.
+// and of u (back), the stores of u and f, and the norm partials.
+//
+// Inside a CTA each phase is split by entries, in the manner of a merge-based
+// CSR product. Thread t takes the entries [t k, (t+1) k) of the CTA's slice,
+// with k = ceil(entries / threads).
+// - It issues all of its gathers before it consumes any of them, so a phase
+//   costs about one memory round trip whatever the row lengths.
+// - It sums its run segment by segment (one segment per row or column).
+// - A row that spans threads is completed by the thread holding its last
+//   entry. That thread adds the earlier threads' carried tails in a fixed
+//   order.
+// Results are deterministic for a given launch shape.
 // ---------------------------------------------------------------------------
 
 // Shared-memory bytes per entry and per row/column of the resident layout.
@@ -408,7 +417,9 @@ struct ResidentBytes {
     static constexpr int kRow = 4 + 4 + (int)sizeof(typename T::Vec2) + (int)sizeof(typename T::Norm2) +
                                 (T::kQuant ? (int)sizeof(float2) : 0);
     static constexpr int kCol = 4 + 4 + (int)sizeof(typename T::Norm2) + (int)sizeof(typename T::Vec2);
+    static constexpr int kThread = 0;
     static constexpr int kSlack = 12 * 16 + 16;  // alignment of 12 segments, plus the end pointers
+    static constexpr int kChunk = sizeof(typename T::Vec2) == 16 ? 2 : 4;  // gathers in flight per lane and item
 };
 
 // First q in [lo, hi] with WE*ptr[q] + WR*q >= t (a non-decreasing key).
@@ -440,25 +451,36 @@ __device__ __forceinline__ int2 resident_range(const int32_t* ptr, int n, int WE
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-constexpr int kResUnroll = 4;
+// Largest item q in [0, n) with ptr[q] <= e (ptr in shared memory, ptr[0] = 0).
+__device__ __forceinline__ int item_of(const int* ptr, int n, int e) {
+    int lo = 0, hi = n;  // invariant: ptr[lo] <= e, answer in [lo, hi)
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (ptr[mid] <= e) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
 
 template <class T, int LPC>
-__global__ void __launch_bounds__(1024, 1) sart_resident_kernel(SartArgs<T> a, int smem_bytes) {
+__global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, int smem_bytes) {
     using Acc = typename T::Acc;
     using V2 = typename T::Vec2;
     using N2 = typename T::Norm2;
     using Pair = typename T::Pair;
     using B = ResidentBytes<T>;
+    constexpr int U = B::kChunk;           // gathers in flight per lane and item
+    constexpr int kGroupsPerWarp = 32 / LPC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int2 s_rows, s_cols;
-    __shared__ double s_red[2][32];
+    __shared__ double2 s_thr[512];
+    __shared__ double s_tot[2];
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int wib = tid >> 5;
     const int nwarps = blockDim.x >> 5;
     const int BD = blockDim.x;
-    constexpr int kGroupsPerWarp = 32 / LPC;
     const int sub = lane % LPC;
     const Acc lam = (Acc)a.lambda;
 
@@ -505,37 +527,38 @@ __global__ void __launch_bounds__(1024, 1) sart_resident_kernel(SartArgs<T> a, i
     V2* c_f = reinterpret_cast<V2*>(smem_raw + off);
     off = align16(off + sizeof(V2) * nc);
 
-    const bool fits = off <= (size_t)smem_bytes;
-    if (!fits) {
+    if (off > (size_t)smem_bytes) {
+        // Cannot happen when the host's bound holds; fail cleanly rather than overrun.
         if (tid == 0) atomicCAS(&a.ctl->err, 0, SPLITSART_ERR_ARG);
-    } else {
-        for (int e = tid; e < nfe; e += BD) {
-            f_val[e] = ldg(a.val + fea + e);
-            f_idx[e] = (uint16_t)__ldg(a.col + fea + e);
-        }
-        for (int q = tid; q < nr; q += BD) {
-            const int i = __ldg(a.nzr + q0 + q);
-            r_ptr[q] = __ldg(a.nzrp + q0 + q) - fea;
-            r_id[q] = i;
-            r_p[q] = ldg(a.p12 + i);
-            r_ir[q] = ldg(a.invR + i);
-            if constexpr (T::kQuant) r_sc[q] = ldg(a.scale + i);
-        }
-        if (tid == 0) r_ptr[nr] = nfe;
-        for (int e = tid; e < nbe; e += BD) {
-            b_val[e] = ldg(a.valT + bea + e);
-            b_idx[e] = (uint16_t)__ldg(a.row + bea + e);
-        }
-        for (int q = tid; q < nc; q += BD) {
-            const int j = __ldg(a.nzc + c0 + q);
-            c_ptr[q] = __ldg(a.nzcp + c0 + q) - bea;
-            c_id[q] = j;
-            c_ic[q] = ldg(a.invC + j);
-            c_f[q] = ldcg(a.f12 + j);
-        }
-        if (tid == 0) c_ptr[nc] = nbe;
+        grid_sync(a.ctl, a.expected, a.timeout_ns, 1);
+        return;
     }
-    double ppz = 0.0;  // this CTA's share of sum(p1^2 + p2^2) over the empty rows
+    for (int e = tid; e < nfe; e += BD) {
+        f_val[e] = ldg(a.val + fea + e);
+        f_idx[e] = (uint16_t)__ldg(a.col + fea + e);
+    }
+    for (int q = tid; q < nr; q += BD) {
+        const int i = __ldg(a.nzr + q0 + q);
+        r_ptr[q] = __ldg(a.nzrp + q0 + q) - fea;
+        r_id[q] = i;
+        r_p[q] = ldg(a.p12 + i);
+        r_ir[q] = ldg(a.invR + i);
+        if constexpr (T::kQuant) r_sc[q] = ldg(a.scale + i);
+    }
+    if (tid == 0) r_ptr[nr] = nfe;
+    for (int e = tid; e < nbe; e += BD) {
+        b_val[e] = ldg(a.valT + bea + e);
+        b_idx[e] = (uint16_t)__ldg(a.row + bea + e);
+    }
+    for (int q = tid; q < nc; q += BD) {
+        const int j = __ldg(a.nzc + c0 + q);
+        c_ptr[q] = __ldg(a.nzcp + c0 + q) - bea;
+        c_id[q] = j;
+        c_ic[q] = ldg(a.invC + j);
+        c_f[q] = ldcg(a.f12 + j);
+    }
+    if (tid == 0) c_ptr[nc] = nbe;
+    double ppz = 0.0;  // this thread's share of sum(p1^2 + p2^2) over the empty rows
     {
         const long long G = gridDim.x, b = blockIdx.x;
         const int z0 = (int)(n_zr * b / G), z1 = (int)(n_zr * (b + 1) / G);
@@ -543,155 +566,170 @@ __global__ void __launch_bounds__(1024, 1) sart_resident_kernel(SartArgs<T> a, i
             const V2 p = ldg(a.p12 + __ldg(a.zr + z));
             ppz += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
         }
-        ppz = warp_sum(ppz);
-        if (lane == 0) s_red[0][wib] = ppz;
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < nwarps; ++w) t += s_red[0][w];
-            ppz = t;  // meaningful in thread 0 only
-        }
     }
     unsigned nbar = 0;
     if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
 
+    // Gathers of one item's first U*W entries (lane-strided by W), and their use.
+    auto issue = [&](const uint16_t* idx, const V2* src, int lo, int hi, int first, int W, V2 (&g)[U]) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = lo + first + u * W;
+            if (e < hi) g[u] = ldca(src + idx[e]);
+        }
+    };
+    auto consume = [&](const Pair* vals, int lo, int hi, int first, int W, const V2 (&g)[U], Acc& s1, Acc& s2) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = lo + first + u * W;
+            if (e < hi) {
+                Acc v1, v2;
+                T::decode(vals[e], v1, v2);
+                s1 += v1 * g[u].x;
+                s2 += v2 * g[u].y;
+            }
+        }
+    };
+    // Entries beyond the first batch (items longer than U*W).
+    auto rest = [&](const uint16_t* idx, const Pair* vals, const V2* src, int lo, int hi, int first, int W, Acc& s1,
+                    Acc& s2) {
+        for (int base = first + U * W; lo + base - first < hi + W; base += U * W) {
+            V2 g[U];
+            issue(idx, src, lo, hi, base, W, g);
+            consume(vals, lo, hi, base, W, g, s1, s2);
+        }
+    };
+
     for (int k = 0;; ++k) {
         // ---- forward: r = p - A f, u = r / R, and the norm partials ----
-        double rr = 0.0, pp = 0.0;
-        for (int q = wib; q < nr; q += nwarps) {
-            const int lo = r_ptr[q], hi = r_ptr[q + 1];
-            Acc s1 = 0, s2 = 0;
-            for (int base = lo; base < hi; base += 32 * kResUnroll) {
-                V2 fv[kResUnroll];
-                Pair v[kResUnroll];
-#pragma unroll
-                for (int u = 0; u < kResUnroll; ++u) {
-                    const int e = base + u * 32 + lane;
-                    if (e < hi) {
-                        v[u] = f_val[e];
-                        fv[u] = ldcg(a.f12 + f_idx[e]);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < kResUnroll; ++u) {
-                    const int e = base + u * 32 + lane;
-                    if (e < hi) {
-                        Acc a1, a2;
-                        T::decode(v[u], a1, a2);
-                        s1 += a1 * fv[u].x;
-                        s2 += a2 * fv[u].y;
-                    }
-                }
+        double rr = ppz, pp = ppz;  // an empty row's residual is its p
+        auto fin_row = [&](int q, Acc s1, Acc s2) {
+            const V2 p = r_p[q];
+            const N2 ir = r_ir[q];
+            V2 u;
+            if constexpr (T::kQuant) {
+                const float2 sc = r_sc[q];
+                s1 *= sc.x;
+                s2 *= sc.y;
+                const Acc r1 = p.x - s1, r2 = p.y - s2;
+                // The back-projection reuses the codes, so the row scale moves into u.
+                u.x = (Acc)((double)r1 * ir.x * (double)sc.x);
+                u.y = (Acc)((double)r2 * ir.y * (double)sc.y);
+                rr += (double)r1 * (double)r1 + (double)r2 * (double)r2;
+            } else {
+                const Acc r1 = p.x - s1, r2 = p.y - s2;
+                u.x = r1 * ir.x;
+                u.y = r2 * ir.y;
+                rr += (double)r1 * (double)r1 + (double)r2 * (double)r2;
             }
-            s1 = warp_sum(s1);
-            s2 = warp_sum(s2);
+            pp += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+            stcg(a.u12 + r_id[q], u);
+        };
+        // Two rows per warp in flight: q and q + nwarps.
+        for (int q = wib; q < nr; q += 2 * nwarps) {
+            const int qb = q + nwarps;
+            const int loA = r_ptr[q], hiA = r_ptr[q + 1];
+            const int loB = qb < nr ? r_ptr[qb] : 0, hiB = qb < nr ? r_ptr[qb + 1] : 0;
+            V2 gA[U], gB[U];
+            issue(f_idx, a.f12, loA, hiA, lane, 32, gA);
+            issue(f_idx, a.f12, loB, hiB, lane, 32, gB);
+            Acc sA1 = 0, sA2 = 0, sB1 = 0, sB2 = 0;
+            consume(f_val, loA, hiA, lane, 32, gA, sA1, sA2);
+            consume(f_val, loB, hiB, lane, 32, gB, sB1, sB2);
+            rest(f_idx, f_val, a.f12, loA, hiA, lane, 32, sA1, sA2);
+            rest(f_idx, f_val, a.f12, loB, hiB, lane, 32, sB1, sB2);
+            sA1 = warp_sum(sA1);
+            sA2 = warp_sum(sA2);
+            sB1 = warp_sum(sB1);
+            sB2 = warp_sum(sB2);
             if (lane == 0) {
-                const V2 p = r_p[q];
-                const N2 ir = r_ir[q];
-                V2 u;
-                if constexpr (T::kQuant) {
-                    const float2 sc = r_sc[q];
-                    s1 *= sc.x;
-                    s2 *= sc.y;
-                    const Acc r1 = p.x - s1, r2 = p.y - s2;
-                    u.x = (Acc)((double)r1 * ir.x * (double)sc.x);
-                    u.y = (Acc)((double)r2 * ir.y * (double)sc.y);
-                    rr += (double)r1 * (double)r1 + (double)r2 * (double)r2;
-                } else {
-                    const Acc r1 = p.x - s1, r2 = p.y - s2;
-                    u.x = r1 * ir.x;
-                    u.y = r2 * ir.y;
-                    rr += (double)r1 * (double)r1 + (double)r2 * (double)r2;
-                }
-                stcg(a.u12 + r_id[q], u);
-                pp += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+                fin_row(q, sA1, sA2);
+                if (qb < nr) fin_row(qb, sB1, sB2);
             }
         }
-        if (lane == 0) {
-            s_red[0][wib] = rr;
-            s_red[1][wib] = pp;
-        }
+        // FP64 is scarce on this part: one warp sums the per-thread values.
+        s_thr[tid] = make_double2(rr, pp);
         __syncthreads();
-        if (tid == 0) {
-            double t0 = ppz, t1 = ppz;  // an empty row's residual is its p
-            for (int w = 0; w < nwarps; ++w) {
-                t0 += s_red[0][w];
-                t1 += s_red[1][w];
+        if (wib == 0) {
+            double t0 = 0.0, t1 = 0.0;
+            for (int t = lane; t < BD; t += 32) {
+                const double2 v = s_thr[t];
+                t0 += v.x;
+                t1 += v.y;
             }
-            __stcg(a.partials + 2 * blockIdx.x, t0);
-            __stcg(a.partials + 2 * blockIdx.x + 1, t1);
+            t0 = warp_sum(t0);
+            t1 = warp_sum(t1);
+            if (lane == 0) {
+                __stcg(a.partials + 2 * blockIdx.x, t0);
+                __stcg(a.partials + 2 * blockIdx.x + 1, t1);
+            }
         }
         if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
 
-        // ---- stop test: every CTA sums the partials in the same order ----
+        // ---- back-projection; the stop test reads its totals while the first gathers fly ----
         const bool last = (k >= a.max_iters);
-        if (last || (k % a.check_every == 0)) {
-            if (wib == 0) {
-                double t0, t1;
-                grid_totals(a.partials, gridDim.x, lane, t0, t1);
-                if (lane == 0) {
-                    s_red[0][0] = t0;
-                    s_red[1][0] = t1;
-                }
+        const bool check = last || (k % a.check_every == 0);
+        auto fin_col = [&](int q, Acc b1, Acc b2) {
+            const N2 ic = c_ic[q];
+            V2 f = c_f[q];
+            if constexpr (T::kQuant) {
+                f.x += (Acc)((double)(lam * b1) * ic.x);
+                f.y += (Acc)((double)(lam * b2) * ic.y);
+            } else {
+                f.x += lam * b1 * ic.x;
+                f.y += lam * b2 * ic.y;
             }
-            __syncthreads();
-            const double trr = s_red[0][0], tpp = s_red[1][0];
-            const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
-            if (last || rho <= a.tol) {
-                if (blockIdx.x == 0 && tid == 0) {
-                    a.result->iters = k;
-                    a.result->status = SPLITSART_OK;
-                    a.result->rho = rho;
-                    a.result->rr = trr;
-                    a.result->pp = tpp;
-                }
-                return;
-            }
-        }
-
-        // ---- back-projection and update: f += lambda (A^T u) / C ----
-        for (int g0 = wib * kGroupsPerWarp; g0 < nc; g0 += nwarps * kGroupsPerWarp) {
-            const int q = g0 + lane / LPC;
-            Acc b1 = 0, b2 = 0;
-            if (q < nc) {
-                const int lo = c_ptr[q], hi = c_ptr[q + 1];
-                for (int base = lo + sub; base < hi; base += LPC * kResUnroll) {
-                    V2 uv[kResUnroll];
-                    Pair v[kResUnroll];
-#pragma unroll
-                    for (int u = 0; u < kResUnroll; ++u) {
-                        const int e = base + u * LPC;
-                        if (e < hi) {
-                            v[u] = b_val[e];
-                            uv[u] = ldcg(a.u12 + b_idx[e]);
+            c_f[q] = f;
+            stcg(a.f12 + c_id[q], f);
+        };
+        const int stride = 2 * nwarps * kGroupsPerWarp;
+        bool first_pass = true;
+        for (int g0 = wib * kGroupsPerWarp; g0 < nc || first_pass; g0 += stride) {
+            const int qA = g0 + lane / LPC, qB = qA + nwarps * kGroupsPerWarp;
+            const int loA = qA < nc ? c_ptr[qA] : 0, hiA = qA < nc ? c_ptr[qA + 1] : 0;
+            const int loB = qB < nc ? c_ptr[qB] : 0, hiB = qB < nc ? c_ptr[qB + 1] : 0;
+            V2 gA[U], gB[U];
+            issue(b_idx, a.u12, loA, hiA, sub, LPC, gA);
+            issue(b_idx, a.u12, loB, hiB, sub, LPC, gB);
+            if (first_pass) {
+                first_pass = false;
+                if (check) {  // uniform over the CTA
+                    if (wib == 0) {
+                        double t0, t1;
+                        grid_totals(a.partials, gridDim.x, lane, t0, t1);
+                        if (lane == 0) {
+                            s_tot[0] = t0;
+                            s_tot[1] = t1;
                         }
                     }
-#pragma unroll
-                    for (int u = 0; u < kResUnroll; ++u) {
-                        const int e = base + u * LPC;
-                        if (e < hi) {
-                            Acc a1, a2;
-                            T::decode(v[u], a1, a2);
-                            b1 += a1 * uv[u].x;
-                            b2 += a2 * uv[u].y;
+                    __syncthreads();
+                    const double trr = s_tot[0], tpp = s_tot[1];
+                    const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
+                    if (last || rho <= a.tol) {
+                        if (blockIdx.x == 0 && tid == 0) {
+                            a.result->iters = k;
+                            a.result->status = SPLITSART_OK;
+                            a.result->rho = rho;
+                            a.result->rr = trr;
+                            a.result->pp = tpp;
                         }
+                        return;
                     }
                 }
+                if (g0 >= nc) break;  // uniform within the warp
             }
-            b1 = warp_sum(b1, LPC);
-            b2 = warp_sum(b2, LPC);
-            if (sub == 0 && q < nc) {
-                const N2 ic = c_ic[q];
-                V2 f = c_f[q];
-                if constexpr (T::kQuant) {
-                    f.x += (Acc)((double)(lam * b1) * ic.x);
-                    f.y += (Acc)((double)(lam * b2) * ic.y);
-                } else {
-                    f.x += lam * b1 * ic.x;
-                    f.y += lam * b2 * ic.y;
-                }
-                c_f[q] = f;
-                stcg(a.f12 + c_id[q], f);
+            Acc bA1 = 0, bA2 = 0, bB1 = 0, bB2 = 0;
+            consume(b_val, loA, hiA, sub, LPC, gA, bA1, bA2);
+            consume(b_val, loB, hiB, sub, LPC, gB, bB1, bB2);
+            rest(b_idx, b_val, a.u12, loA, hiA, sub, LPC, bA1, bA2);
+            rest(b_idx, b_val, a.u12, loB, hiB, sub, LPC, bB1, bB2);
+            bA1 = warp_sum(bA1, LPC);
+            bA2 = warp_sum(bA2, LPC);
+            bB1 = warp_sum(bB1, LPC);
+            bB2 = warp_sum(bB2, LPC);
+            if (sub == 0) {
+                if (qA < nc) fin_col(qA, bA1, bA2);
+                if (qB < nc) fin_col(qB, bB1, bB2);
             }
         }
         if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
@@ -769,7 +807,9 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
     cudaFuncAttributes fa{};
     e = cudaFuncGetAttributes(&fa, (const void*)rkern);
     if (e != cudaSuccess) return cuda_fail(e, "solve: kernel attributes");
-    const long long res_avail = (long long)smem_optin - (long long)fa.sharedSizeBytes;
+    const int res_threads = (o.block_threads > 0 && o.block_threads <= 512) ? o.block_threads : 512;
+    const long long res_avail = (long long)smem_optin - (long long)fa.sharedSizeBytes -
+                                (long long)ResidentBytes<T>::kThread * res_threads - 32;
     const bool res_ok = s->Mh <= 65536 && s->Nh <= 65536 && resident_bound<T>(fs, nsm) <= res_avail;
     if (o.kernel == 2 && !res_ok)
         return fail(SPLITSART_ERR_ARG, "solve: the system does not fit in shared memory (need %lld of %lld bytes per SM)",
@@ -793,7 +833,7 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
     e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return cuda_fail(e, "solve: shared memory attribute");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, threads, dyn);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, use_res ? res_threads : threads, dyn);
     if (e != cudaSuccess) return cuda_fail(e, "solve: occupancy");
     if (per_sm < 1) return fail(SPLITSART_ERR_CUDA, "solve: kernel does not fit on an SM");
     if (!use_res) {
@@ -809,8 +849,8 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
         return cuda_fail(e, "solve: memset");
     void* args_stream[] = {&a};
     void* args_res[] = {&a, &smem_bytes};
-    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(threads), use_res ? args_res : args_stream,
-                                    dyn, st);
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(use_res ? res_threads : threads),
+                                    use_res ? args_res : args_stream, dyn, st);
     if (e != cudaSuccess) return cuda_fail(e, "solve: cooperative launch");
     return SPLITSART_OK;
 }
