@@ -148,20 +148,50 @@ void splitsart_geometry_destroy(splitsart_geometry* g);
 int splitsart_fold_system(const splitsart_geometry* g, int dtype, void* stream, splitsart_system** out);
 
 /*
+ * Fold a batch of independent slices into one system. Each slice is one
+ * geometry, with its own sizes, and satisfies Eq. (2) by itself.
+ * The slices are concatenated in every index space:
+ * - folded rows and columns;
+ * - full projections p (slice k at M_off[k]);
+ * - full images f (slice k at N_off[k]).
+ * The folded matrix is block-diagonal, so the slices stay independent.
+ * fold_rhs, fold_image, recombine and project act on all slices at once.
+ * splitsart_solve runs every slice in one persistent launch, and each slice
+ * has its own stopping test: rho_s of its own residual, its own iteration
+ * count and its own returned iterate. Read them with
+ * splitsart_solve_result_slices.
+ * geoms: array of nslices geometry handles (borrowed; the data are copied).
+ */
+int splitsart_fold_batch(const splitsart_geometry* const* geoms, int nslices, int dtype, void* stream,
+                         splitsart_system** out);
+
+/*
+ * Slice offsets. Each array has nslices + 1 entries, or is NULL to skip it.
+ * - M_off: full projections;
+ * - N_off: full images;
+ * - Mh_off: folded rows;
+ * - Nh_off: folded columns.
+ */
+int splitsart_system_slices(const splitsart_system* sys, int64_t* M_off, int64_t* N_off, int64_t* Mh_off,
+                            int64_t* Nh_off);
+
+/*
  * Re-run the device fold of an existing system from its uploaded half rows.
  * The fold covers the CSR, the CSC and the normalisers. Nothing is allocated.
  */
 int splitsart_refold(splitsart_system* sys, void* stream);
 
 typedef struct splitsart_system_info {
-    int64_t M, N, Mh, Nh;
+    int64_t M, N, Mh, Nh;   /* totals over all slices */
     int64_t nnz_half;    /* stored entries of rows 0..Mh-1 of A */
     int64_t S;           /* stored entries of the shared folded pattern */
     int64_t empty_rows;  /* folded rows with no entry */
     int64_t exact_zeros; /* entries with w1 = 0 made by cancellation */
     int32_t dtype;
-    int32_t nx, nz;      /* 0 when the geometry came from a CSR */
+    int32_t nx, nz;      /* 0 when the geometry came from a CSR, or for a batch */
     int64_t device_bytes;
+    int32_t nslices;     /* 1, or the slices of a batch */
+    int32_t reserved;
 } splitsart_system_info;
 
 /* Fill *info. This synchronises with the system's last stream, once, to read S. */
@@ -326,6 +356,13 @@ int splitsart_solve_static(int64_t Mh, int64_t Nh, const int32_t* rp_dev, const 
                            const int32_t* cp_dev, const int32_t* row_dev, const void* valT_dev, const void* invR_dev,
                            const void* invC_dev, const void* p12_dev, void* f12_dev, const splitsart_solve_opts* opts,
                            splitsart_solve_info* info_dev, void* stream);
+
+/*
+ * Per-slice results of the last solve of a batch system. info has at least
+ * nslices entries. Synchronises like splitsart_solve_result. A single-slice
+ * system reports its one result.
+ */
+int splitsart_solve_result_slices(splitsart_system* sys, splitsart_solve_info* info, int n);
 
 /* Copy the thread's last error message into buf (truncated, NUL-terminated). Returns its full length. */
 int splitsart_last_error(char* buf, size_t len);

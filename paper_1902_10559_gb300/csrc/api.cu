@@ -121,6 +121,31 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 using namespace splitsart;
 
+extern "C" int splitsart_solve_result_slices(splitsart_system* s, splitsart_solve_info* info, int n) {
+    if (!s || !info || n < s->ns) return fail(SPLITSART_ERR_ARG, "solve_result_slices: NULL or short buffer");
+    splitsart_solve_info agg;
+    int rc = splitsart_solve_result(s, &agg);
+    if (rc != SPLITSART_OK) {
+        for (int k = 0; k < s->ns; ++k) info[k] = agg;
+        return rc;
+    }
+    if (s->ns == 1) {
+        info[0] = agg;
+        return SPLITSART_OK;
+    }
+    std::vector<SliceSolve> v(s->ns);
+    cudaError_t e = cudaMemcpy(v.data(), s->sl_solve, sizeof(SliceSolve) * s->ns, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "solve_result_slices: read");
+    for (int k = 0; k < s->ns; ++k) {
+        info[k].iters = v[k].iters;
+        info[k].status = v[k].done ? SPLITSART_OK : SPLITSART_ERR_STATE;
+        info[k].rho = v[k].rho;
+        info[k].rr = v[k].rr;
+        info[k].pp = v[k].pp;
+    }
+    return SPLITSART_OK;
+}
+
 extern "C" int splitsart_last_error(char* buf, size_t len) {
     if (buf && len) {
         std::strncpy(buf, g_last_error.c_str(), len - 1);
@@ -131,20 +156,38 @@ extern "C" int splitsart_last_error(char* buf, size_t len) {
 
 extern "C" const char* splitsart_version(void) { return "splitsart 0.1 (sm_103a)"; }
 
-extern "C" int splitsart_fold_system(const splitsart_geometry* g, int dtype, void* stream, splitsart_system** out) {
-    if (!g || !out) return fail(SPLITSART_ERR_ARG, "fold_system: NULL argument");
+namespace {
+
+// Build one device system from ns geometries (ns = 1: a single slice; more: a
+// block-diagonal batch). Each slice keeps its own M_s, N_s and reflection.
+int create_system(const splitsart_geometry* const* geoms, int ns, int dtype, cudaStream_t st, splitsart_system** out) {
+    if (!geoms || !out || ns < 1) return fail(SPLITSART_ERR_ARG, "fold: NULL argument or no slices");
     *out = nullptr;
-    if (dtype < SPLITSART_F64 || dtype > SPLITSART_F16) return fail(SPLITSART_ERR_ARG, "fold_system: bad dtype %d", dtype);
-    const HalfCsr& h = g->half;
-    const int64_t M = h.M, N = h.N, Mh = M / 2, Nh = N / 2, nnz = h.row_ptr.back();
-    if (nnz >= INT32_MAX) return fail(SPLITSART_ERR_ARG, "fold_system: %lld half-row entries exceed int32", (long long)nnz);
-    if (Mh >= INT32_MAX || Nh >= INT32_MAX) return fail(SPLITSART_ERR_ARG, "fold_system: dimensions exceed int32");
-    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype < SPLITSART_F64 || dtype > SPLITSART_F16) return fail(SPLITSART_ERR_ARG, "fold: bad dtype %d", dtype);
+    std::vector<long long> rows(ns + 1, 0), cols(ns + 1, 0), Mo(ns + 1, 0), No(ns + 1, 0), nnzo(ns + 1, 0);
+    std::vector<int> nxs(ns, 0), nzs(ns, 0);
+    for (int k = 0; k < ns; ++k) {
+        const splitsart_geometry* g = geoms[k];
+        if (!g) return fail(SPLITSART_ERR_ARG, "fold: NULL geometry %d", k);
+        const HalfCsr& h = g->half;
+        rows[k + 1] = rows[k] + h.M / 2;
+        cols[k + 1] = cols[k] + h.N / 2;
+        Mo[k + 1] = Mo[k] + h.M;
+        No[k + 1] = No[k] + h.N;
+        nnzo[k + 1] = nnzo[k] + h.row_ptr.back();
+        if (g->has_params) {
+            nxs[k] = g->params.nx;
+            nzs[k] = g->params.nz;
+        }
+    }
+    const int64_t M = Mo[ns], N = No[ns], Mh = rows[ns], Nh = cols[ns], nnz = nnzo[ns];
+    if (nnz >= INT32_MAX) return fail(SPLITSART_ERR_ARG, "fold: %lld half-row entries exceed int32", (long long)nnz);
+    if (Mh >= INT32_MAX || Nh >= INT32_MAX) return fail(SPLITSART_ERR_ARG, "fold: dimensions exceed int32");
     int rc = check_stream_ok(st);
     if (rc) return rc;
 
     auto* s = new (std::nothrow) splitsart_system();
-    if (!s) return fail(SPLITSART_ERR_NOMEM, "fold_system: out of host memory");
+    if (!s) return fail(SPLITSART_ERR_NOMEM, "fold: out of host memory");
     s->M = M;
     s->N = N;
     s->Mh = Mh;
@@ -152,9 +195,16 @@ extern "C" int splitsart_fold_system(const splitsart_geometry* g, int dtype, voi
     s->nnz_half = nnz;
     s->dtype = dtype;
     s->last = st;
-    if (g->has_params) {
-        s->nx = g->params.nx;
-        s->nz = g->params.nz;
+    s->ns = ns;
+    s->h_rows = rows;
+    s->h_cols = cols;
+    s->h_M = Mo;
+    s->h_N = No;
+    s->h_nx = nxs;
+    s->h_nz = nzs;
+    if (ns == 1) {
+        s->nx = nxs[0];
+        s->nz = nzs[0];
     }
     const size_t pb = pair_bytes(dtype), nb = norm_pair_bytes(dtype), vb = vec_pair_bytes(dtype);
     const int64_t mx = (Mh > Nh ? Mh : Nh) + 1;
@@ -181,6 +231,15 @@ extern "C" int splitsart_fold_system(const splitsart_geometry* g, int dtype, voi
         {(void**)&s->zr, sizeof(int32_t) * (Mh + 1)},
         {(void**)&s->nzc, sizeof(int32_t) * (Nh + 1)},
         {(void**)&s->nzcp, sizeof(int32_t) * (Nh + 1)},
+        {(void**)&s->sl_rows, sizeof(long long) * (ns + 1)},
+        {(void**)&s->sl_cols, sizeof(long long) * (ns + 1)},
+        {(void**)&s->sl_M, sizeof(long long) * (ns + 1)},
+        {(void**)&s->sl_N, sizeof(long long) * (ns + 1)},
+        {(void**)&s->sl_nx, sizeof(int) * ns},
+        {(void**)&s->sl_nz, sizeof(int) * ns},
+        {(void**)&s->sl_solve, sizeof(SliceSolve) * ns},
+        {(void**)&s->rr_row, ns > 1 ? sizeof(double) * Mh : 0},
+        {(void**)&s->ndone, sizeof(int) * 4},
         {(void**)&s->cnt, sizeof(int32_t) * mx},
         {(void**)&s->flags, sizeof(int32_t) * mx},
         {(void**)&s->scan_tmp, sizeof(int32_t) * ntiles},
@@ -198,8 +257,7 @@ extern "C" int splitsart_fold_system(const splitsart_geometry* g, int dtype, voi
     if (e != cudaSuccess) {
         delete s;
         cudaGetLastError();
-        return fail(SPLITSART_ERR_NOMEM, "fold_system: cudaMalloc of %zu bytes failed (%s)", total,
-                    cudaGetErrorString(e));
+        return fail(SPLITSART_ERR_NOMEM, "fold: cudaMalloc of %zu bytes failed (%s)", total, cudaGetErrorString(e));
     }
     s->device_bytes = (int64_t)total;
     size_t off = 0;
@@ -207,11 +265,32 @@ extern "C" int splitsart_fold_system(const splitsart_geometry* g, int dtype, voi
         *it.ptr = it.bytes > 0 ? (void*)((char*)s->base + off) : nullptr;
         off += align_up(it.bytes > 0 ? it.bytes : 1);
     }
-    if ((e = cudaMemcpyAsync(s->hrp, h.row_ptr.data(), sizeof(int64_t) * (Mh + 1), cudaMemcpyHostToDevice, st)) ||
-        (nnz && (e = cudaMemcpyAsync(s->hcol, h.col.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st))) ||
-        (nnz && (e = cudaMemcpyAsync(s->hval, h.val.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, st)))) {
+    // Upload: one row-pointer array over all slices, then each slice's entries in place.
+    std::vector<int64_t> hrp(Mh + 1);
+    for (int k = 0; k < ns; ++k) {
+        const HalfCsr& h = geoms[k]->half;
+        for (int64_t i = 0; i < h.M / 2; ++i) hrp[rows[k] + i] = nnzo[k] + h.row_ptr[i];
+    }
+    hrp[Mh] = nnz;
+    e = cudaMemcpyAsync(s->hrp, hrp.data(), sizeof(int64_t) * (Mh + 1), cudaMemcpyHostToDevice, st);
+    for (int k = 0; k < ns && e == cudaSuccess; ++k) {
+        const HalfCsr& h = geoms[k]->half;
+        const int64_t n = nnzo[k + 1] - nnzo[k];
+        if (n == 0) continue;
+        e = cudaMemcpyAsync(s->hcol + nnzo[k], h.col.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->hval + nnzo[k], h.val.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->sl_rows, rows.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->sl_cols, cols.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->sl_M, Mo.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->sl_N, No.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->sl_nx, nxs.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->sl_nz, nzs.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st);
+    // The host vectors above are pageable: the copies complete before cudaMemcpyAsync returns.
+    if (e != cudaSuccess) {
         splitsart_system_destroy(s);
-        return cuda_fail(e, "fold_system: upload");
+        return cuda_fail(e, "fold: upload");
     }
     rc = run_fold(s, st);
     if (rc) {
@@ -219,6 +298,30 @@ extern "C" int splitsart_fold_system(const splitsart_geometry* g, int dtype, voi
         return rc;
     }
     *out = s;
+    return SPLITSART_OK;
+}
+
+}  // namespace
+
+extern "C" int splitsart_fold_system(const splitsart_geometry* g, int dtype, void* stream, splitsart_system** out) {
+    if (!g) return fail(SPLITSART_ERR_ARG, "fold_system: NULL geometry");
+    return create_system(&g, 1, dtype, (cudaStream_t)stream, out);
+}
+
+extern "C" int splitsart_fold_batch(const splitsart_geometry* const* geoms, int nslices, int dtype, void* stream,
+                                    splitsart_system** out) {
+    return create_system(geoms, nslices, dtype, (cudaStream_t)stream, out);
+}
+
+extern "C" int splitsart_system_slices(const splitsart_system* s, int64_t* M_off, int64_t* N_off, int64_t* Mh_off,
+                                       int64_t* Nh_off) {
+    if (!s) return fail(SPLITSART_ERR_ARG, "system_slices: NULL system");
+    for (int k = 0; k <= s->ns; ++k) {
+        if (M_off) M_off[k] = s->h_M[k];
+        if (N_off) N_off[k] = s->h_N[k];
+        if (Mh_off) Mh_off[k] = s->h_rows[k];
+        if (Nh_off) Nh_off[k] = s->h_cols[k];
+    }
     return SPLITSART_OK;
 }
 
@@ -257,6 +360,8 @@ extern "C" int splitsart_system_info_get(splitsart_system* s, splitsart_system_i
     info->nx = s->nx;
     info->nz = s->nz;
     info->device_bytes = s->device_bytes;
+    info->nslices = s->ns;
+    info->reserved = 0;
     return SPLITSART_OK;
 }
 
@@ -317,8 +422,9 @@ extern "C" int splitsart_fold_rhs(const splitsart_system* s, const void* p, void
 static int check_layout(const splitsart_system* s, int layout, const char* who) {
     if (layout == SPLITSART_LAYOUT_SNAKE) return SPLITSART_OK;
     if (layout == SPLITSART_LAYOUT_IMAGE) {
-        if (s->nx <= 0 || s->nz <= 0)
-            return fail(SPLITSART_ERR_ARG, "%s: image layout needs a geometry built from parameters", who);
+        for (int k = 0; k < s->ns; ++k)
+            if (s->h_nx[k] <= 0 || s->h_nz[k] <= 0)
+                return fail(SPLITSART_ERR_ARG, "%s: image layout needs geometries built from parameters", who);
         return SPLITSART_OK;
     }
     return fail(SPLITSART_ERR_ARG, "%s: unknown layout %d", who, layout);

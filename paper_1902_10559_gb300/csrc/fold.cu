@@ -58,11 +58,24 @@ __device__ __forceinline__ void for_each_folded(const int32_t* __restrict__ hcol
     }
 }
 
-__global__ void fold_count_kernel(int64_t Mh, int N, const int64_t* __restrict__ hrp,
+// The slice holding global index i: the largest s with off[s] <= i.
+__device__ __forceinline__ int slice_of(const long long* off, int ns, long long i) {
+    int lo = 0, hi = ns;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void fold_count_kernel(int64_t Mh, SliceMap sm, const int64_t* __restrict__ hrp,
                                   const int32_t* __restrict__ hcol, const double* __restrict__ hval,
                                   int32_t* __restrict__ cnt) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= Mh) return;
+    const int s = slice_of(sm.rows, sm.ns, i);
+    const int N = (int)(sm.N[s + 1] - sm.N[s]);
     int n = 0;
     for_each_folded(hcol, hval, hrp[i], hrp[i + 1], N, [&](int, double, double) { ++n; });
     cnt[i] = n;
@@ -186,7 +199,7 @@ __device__ __forceinline__ void store_pair(typename T::Pair* p, double a1, doubl
 }
 
 template <class T>
-__global__ void fold_fill_kernel(int64_t Mh, int N, const int64_t* __restrict__ hrp,
+__global__ void fold_fill_kernel(int64_t Mh, SliceMap sm, const int64_t* __restrict__ hrp,
                                  const int32_t* __restrict__ hcol, const double* __restrict__ hval,
                                  const int32_t* __restrict__ frp, int32_t* __restrict__ col,
                                  typename T::Pair* __restrict__ val, double2* __restrict__ Rsum,
@@ -194,6 +207,9 @@ __global__ void fold_fill_kernel(int64_t Mh, int N, const int64_t* __restrict__ 
                                  FoldStats* __restrict__ stats) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= Mh) return;
+    const int sl = slice_of(sm.rows, sm.ns, i);
+    const int N = (int)(sm.N[sl + 1] - sm.N[sl]);
+    const int col_base = (int)sm.cols[sl];  // folded columns of this slice start here
     const int64_t e0 = hrp[i], e1 = hrp[i + 1];
     float s1 = 0.f, s2 = 0.f;
     if constexpr (T::kQuant) {
@@ -212,7 +228,7 @@ __global__ void fold_fill_kernel(int64_t Mh, int N, const int64_t* __restrict__ 
     for_each_folded(hcol, hval, e0, e1, N, [&](int c, double wd, double wr) {
         const double a1 = wd - wr, a2 = wd + wr;
         zeros += (a1 == 0.0);
-        col[out] = c;
+        col[out] = col_base + c;
         double d1, d2;
         store_pair<T>(&val[out], a1, a2, s1, s2, d1, d2);
         R1 += fabs(d1);
@@ -336,15 +352,15 @@ int fold_typed(splitsart_system* s, cudaStream_t st) {
     using Pair = typename T::Pair;
     using N2 = typename T::Norm2;
     const int64_t Mh = s->Mh, Nh = s->Nh;
-    const int N = (int)s->N;
     cudaError_t e;
     if ((e = cudaMemsetAsync(s->stats, 0, sizeof(FoldStats), st)) != cudaSuccess) return cuda_fail(e, "fold memset");
-    if (Mh > 0) fold_count_kernel<<<(unsigned)((Mh + 255) / 256), 256, 0, st>>>(Mh, N, s->hrp, s->hcol, s->hval, s->cnt);
+    const SliceMap sm = slice_map(s);
+    if (Mh > 0) fold_count_kernel<<<(unsigned)((Mh + 255) / 256), 256, 0, st>>>(Mh, sm, s->hrp, s->hcol, s->hval, s->cnt);
     int rc = exclusive_scan(s->cnt, s->rp, s->scan_tmp, Mh, st);
     if (rc) return rc;
     if (Mh > 0)
         fold_fill_kernel<T><<<(unsigned)((Mh + 127) / 128), 128, 0, st>>>(
-            Mh, N, s->hrp, s->hcol, s->hval, s->rp, s->col, (Pair*)s->val, s->Rsum, (N2*)s->invR, s->scale,
+            Mh, sm, s->hrp, s->hcol, s->hval, s->rp, s->col, (Pair*)s->val, s->Rsum, (N2*)s->invR, s->scale,
             s->stats);
     rc = compact(s->rp, Mh, s->flags, s->cnt, s->scan_tmp, s->nzr, s->nzrp, s->zr, &s->stats->n_nzr,
                  &s->stats->n_zr, st);
@@ -371,7 +387,7 @@ int fold_typed(splitsart_system* s, cudaStream_t st) {
     return SPLITSART_OK;
 }
 
-// ---- vector kernels ----
+// ---- vector kernels (all slices at once; each index finds its slice) ----
 
 __device__ __forceinline__ int64_t image_index(int64_t j, int nx, int nz) {
     const int64_t c = j / nz, q = j % nz;
@@ -379,38 +395,60 @@ __device__ __forceinline__ int64_t image_index(int64_t j, int nx, int nz) {
     return r * nx + c;
 }
 
+// Positions in the full image vector of folded column j and of its mirror.
+__device__ __forceinline__ void image_pair(const SliceMap& sm, int layout, int64_t j, int64_t& a_idx, int64_t& b_idx) {
+    const int s = slice_of(sm.cols, sm.ns, j);
+    const int64_t lj = j - sm.cols[s];
+    const int64_t Ns = sm.N[s + 1] - sm.N[s], base = sm.N[s];
+    const int64_t lm = Ns - 1 - lj;
+    if (layout == SPLITSART_LAYOUT_IMAGE) {
+        a_idx = base + image_index(lj, sm.nx[s], sm.nz[s]);
+        b_idx = base + image_index(lm, sm.nx[s], sm.nz[s]);
+    } else {
+        a_idx = base + lj;
+        b_idx = base + lm;
+    }
+}
+
+// Positions in the full projection vector of folded row i and of its mirror ray.
+__device__ __forceinline__ void ray_pair(const SliceMap& sm, int64_t i, int64_t& a_idx, int64_t& b_idx) {
+    const int s = slice_of(sm.rows, sm.ns, i);
+    const int64_t li = i - sm.rows[s];
+    const int64_t Ms = sm.M[s + 1] - sm.M[s], base = sm.M[s];
+    a_idx = base + li;
+    b_idx = base + Ms - 1 - li;
+}
+
 template <class V, class V2>
-__global__ void fold_rhs_kernel(int64_t M, const V* __restrict__ p, V2* __restrict__ p12) {
+__global__ void fold_rhs_kernel(int64_t Mh, SliceMap sm, const V* __restrict__ p, V2* __restrict__ p12) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= M / 2) return;
-    const V a = p[i], b = p[M - 1 - i];
+    if (i >= Mh) return;
+    int64_t ia, ib;
+    ray_pair(sm, i, ia, ib);
+    const V a = p[ia], b = p[ib];
     p12[i] = V2{a - b, a + b};
 }
 
 template <class V, class V2>
-__global__ void fold_image_kernel(int64_t N, int layout, int nx, int nz, const V* __restrict__ f,
-                                  V2* __restrict__ f12) {
+__global__ void fold_image_kernel(int64_t Nh, SliceMap sm, int layout, const V* __restrict__ f, V2* __restrict__ f12) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= N / 2) return;
-    const int64_t jm = N - 1 - j;
-    const int64_t a_idx = layout == SPLITSART_LAYOUT_IMAGE ? image_index(j, nx, nz) : j;
-    const int64_t b_idx = layout == SPLITSART_LAYOUT_IMAGE ? image_index(jm, nx, nz) : jm;
-    const V a = f[a_idx], b = f[b_idx];
+    if (j >= Nh) return;
+    int64_t ia, ib;
+    image_pair(sm, layout, j, ia, ib);
+    const V a = f[ia], b = f[ib];
     f12[j] = V2{a - b, a + b};
 }
 
 // Theorem 1, Eq. (5).
 template <class V, class V2>
-__global__ void recombine_kernel(int64_t N, int layout, int nx, int nz, const V2* __restrict__ f12,
-                                 V* __restrict__ f) {
+__global__ void recombine_kernel(int64_t Nh, SliceMap sm, int layout, const V2* __restrict__ f12, V* __restrict__ f) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= N / 2) return;
+    if (j >= Nh) return;
     const V2 v = f12[j];
-    const int64_t jm = N - 1 - j;
-    const int64_t a_idx = layout == SPLITSART_LAYOUT_IMAGE ? image_index(j, nx, nz) : j;
-    const int64_t b_idx = layout == SPLITSART_LAYOUT_IMAGE ? image_index(jm, nx, nz) : jm;
-    f[a_idx] = (v.y + v.x) / V(2);
-    f[b_idx] = (v.y - v.x) / V(2);
+    int64_t ia, ib;
+    image_pair(sm, layout, j, ia, ib);
+    f[ia] = (v.y + v.x) / V(2);
+    f[ib] = (v.y - v.x) / V(2);
 }
 
 // q = (A1 f1, A2 f2): one warp per folded row.
@@ -444,12 +482,14 @@ __global__ void spmv_pairs_kernel(int64_t Mh, const int32_t* __restrict__ rp, co
 
 // p_i = (q2 + q1)/2, p_{M-1-i} = (q2 - q1)/2: the fold of p, inverted.
 template <class V, class V2>
-__global__ void unfold_rays_kernel(int64_t M, const V2* __restrict__ q12, V* __restrict__ p) {
+__global__ void unfold_rays_kernel(int64_t Mh, SliceMap sm, const V2* __restrict__ q12, V* __restrict__ p) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= M / 2) return;
+    if (i >= Mh) return;
     const V2 q = q12[i];
-    p[i] = (q.y + q.x) / V(2);
-    p[M - 1 - i] = (q.y - q.x) / V(2);
+    int64_t ia, ib;
+    ray_pair(sm, i, ia, ib);
+    p[ia] = (q.y + q.x) / V(2);
+    p[ib] = (q.y - q.x) / V(2);
 }
 
 template <class T>
@@ -457,13 +497,14 @@ int project_typed(splitsart_system* s, const void* f, int layout, void* p, cudaS
     using V = typename T::Acc;
     using V2 = typename T::Vec2;
     const int64_t Nh = s->Nh, Mh = s->Mh;
+    const SliceMap sm = slice_map(s);
     if (Nh > 0)
-        fold_image_kernel<V, V2><<<(unsigned)((Nh + 255) / 256), 256, 0, st>>>(s->N, layout, s->nx, s->nz,
-                                                                              (const V*)f, (V2*)s->tmp_f12);
+        fold_image_kernel<V, V2><<<(unsigned)((Nh + 255) / 256), 256, 0, st>>>(Nh, sm, layout, (const V*)f,
+                                                                              (V2*)s->tmp_f12);
     if (Mh > 0) {
         spmv_pairs_kernel<T><<<(unsigned)((Mh * 32 + 255) / 256), 256, 0, st>>>(
             Mh, s->rp, s->col, (const typename T::Pair*)s->val, s->scale, (const V2*)s->tmp_f12, (V2*)s->tmp_q12);
-        unfold_rays_kernel<V, V2><<<(unsigned)((Mh + 255) / 256), 256, 0, st>>>(s->M, (const V2*)s->tmp_q12, (V*)p);
+        unfold_rays_kernel<V, V2><<<(unsigned)((Mh + 255) / 256), 256, 0, st>>>(Mh, sm, (const V2*)s->tmp_q12, (V*)p);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SPLITSART_OK : cuda_fail(e, "project launch");
@@ -485,8 +526,9 @@ int run_fold_rhs(const splitsart_system* s, const void* p, void* p12, cudaStream
     const int64_t Mh = s->Mh;
     if (Mh == 0) return SPLITSART_OK;
     const unsigned g = (unsigned)((Mh + 255) / 256);
-    if (s->dtype == SPLITSART_F64) fold_rhs_kernel<double, double2><<<g, 256, 0, st>>>(s->M, (const double*)p, (double2*)p12);
-    else fold_rhs_kernel<float, float2><<<g, 256, 0, st>>>(s->M, (const float*)p, (float2*)p12);
+    const SliceMap sm = slice_map(s);
+    if (s->dtype == SPLITSART_F64) fold_rhs_kernel<double, double2><<<g, 256, 0, st>>>(Mh, sm, (const double*)p, (double2*)p12);
+    else fold_rhs_kernel<float, float2><<<g, 256, 0, st>>>(Mh, sm, (const float*)p, (float2*)p12);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SPLITSART_OK : cuda_fail(e, "fold_rhs launch");
 }
@@ -495,10 +537,11 @@ int run_fold_image(const splitsart_system* s, const void* f, int layout, void* f
     const int64_t Nh = s->Nh;
     if (Nh == 0) return SPLITSART_OK;
     const unsigned g = (unsigned)((Nh + 255) / 256);
+    const SliceMap sm = slice_map(s);
     if (s->dtype == SPLITSART_F64)
-        fold_image_kernel<double, double2><<<g, 256, 0, st>>>(s->N, layout, s->nx, s->nz, (const double*)f, (double2*)f12);
+        fold_image_kernel<double, double2><<<g, 256, 0, st>>>(Nh, sm, layout, (const double*)f, (double2*)f12);
     else
-        fold_image_kernel<float, float2><<<g, 256, 0, st>>>(s->N, layout, s->nx, s->nz, (const float*)f, (float2*)f12);
+        fold_image_kernel<float, float2><<<g, 256, 0, st>>>(Nh, sm, layout, (const float*)f, (float2*)f12);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SPLITSART_OK : cuda_fail(e, "fold_image launch");
 }
@@ -507,10 +550,11 @@ int run_recombine(const splitsart_system* s, const void* f12, void* f, int layou
     const int64_t Nh = s->Nh;
     if (Nh == 0) return SPLITSART_OK;
     const unsigned g = (unsigned)((Nh + 255) / 256);
+    const SliceMap sm = slice_map(s);
     if (s->dtype == SPLITSART_F64)
-        recombine_kernel<double, double2><<<g, 256, 0, st>>>(s->N, layout, s->nx, s->nz, (const double2*)f12, (double*)f);
+        recombine_kernel<double, double2><<<g, 256, 0, st>>>(Nh, sm, layout, (const double2*)f12, (double*)f);
     else
-        recombine_kernel<float, float2><<<g, 256, 0, st>>>(s->N, layout, s->nx, s->nz, (const float2*)f12, (float*)f);
+        recombine_kernel<float, float2><<<g, 256, 0, st>>>(Nh, sm, layout, (const float2*)f12, (float*)f);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SPLITSART_OK : cuda_fail(e, "recombine launch");
 }

@@ -75,7 +75,32 @@ struct SartArgs {
     int tile_entries;   // TE
     int direct_rows;    // kDirect only: Mh (nzrp = rp, row q is row q, no empty-row list)
     int direct_cols;    // kDirect only: Nh (nzcp = cp, column q is column q)
+    // kBatch only: slices with their own stopping tests.
+    int ns;
+    const long long* sl_rows;  // [ns+1] folded-row prefix
+    const long long* sl_cols;  // [ns+1] folded-column prefix
+    SliceSolve* sl_solve;      // [ns]
+    double* rr_row;            // [Mh] per-row residual^2
+    int* ndone;                // slices finished
 };
+
+// The slice holding global index i (largest s with off[s] <= i).
+__device__ __forceinline__ int slice_index(const long long* off, int ns, long long i) {
+    int lo = 0, hi = ns;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// One warp: sum of v[lo..hi) in a fixed order (lane-strided, then a shuffle tree).
+__device__ __forceinline__ double warp_sum_range(const double* v, long long lo, long long hi, int lane) {
+    double t = 0.0;
+    for (long long i = lo + lane; i < hi; i += 32) t += __ldcg(v + i);
+    return warp_sum(t);
+}
 
 // Warp-cooperative search: the first q in [lo, hi] with ptr[q] >= t, where
 // ptr is non-decreasing and q = hi if no probed index qualifies. Only indices
@@ -123,7 +148,9 @@ __device__ int plan_tiles(const int32_t* ptr, int n, int TE, int* tiles, int lan
 
 // kDirect: the caller's plain folded CSR/CSC is used as is (no compacted
 // lists). Empty rows then pass through the row loop with no entries.
-template <class T, int LPC, bool kDirect = false>
+// kBatch: the system is a block-diagonal batch of independent slices, each
+// with its own stopping test (per-slice rho, iteration count and done flag).
+template <class T, int LPC, bool kDirect = false, bool kBatch = false>
 __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
     using Acc = typename T::Acc;
     using V2 = typename T::Vec2;
@@ -180,6 +207,26 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
         }
     }
     unsigned nbar = 0;
+    const int gw = blockIdx.x * nwarps + wib, nw_grid = gridDim.x * nwarps;
+    if constexpr (kBatch) {
+        // Empty rows keep residual p; each slice's ||p||^2 is summed once.
+        const long long Mh = a.sl_rows[a.ns];
+        for (int z = blockIdx.x * BD + tid; z < n_zr; z += gridDim.x * BD) {
+            const int i = __ldg(a.zr + z);
+            const V2 p = ldg(a.p12 + i);
+            a.rr_row[i] = (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+        }
+        for (int sl = gw; sl < a.ns; sl += nw_grid) {
+            double t = 0.0;
+            for (long long i = __ldg(a.sl_rows + sl) + lane; i < __ldg(a.sl_rows + sl + 1); i += 32) {
+                const V2 p = ldg(a.p12 + i);
+                t += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+            }
+            t = warp_sum(t);
+            if (lane == 0) a.sl_solve[sl] = SliceSolve{-1, 0, 0.0, 0.0, t};
+        }
+        (void)Mh;
+    }
     if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     const int nrt = s_nrt, nct = s_nct;
 
@@ -262,8 +309,12 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
                         u.y = r2 * ir.y;
                     }
                     stcg(a.u12 + i, u);
-                    rr += (double)r1 * (double)r1 + (double)r2 * (double)r2;
-                    pp += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+                    if constexpr (kBatch) {
+                        __stcg(a.rr_row + i, (double)r1 * (double)r1 + (double)r2 * (double)r2);
+                    } else {
+                        rr += (double)r1 * (double)r1 + (double)r2 * (double)r2;
+                        pp += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+                    }
                 }
             }
             __syncthreads();  // prod is reused by the next tile
@@ -284,9 +335,34 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
         }
         if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
 
-        // ---- stop test: every CTA sums the partials in the same order ----
         const bool last = (k >= a.max_iters);
-        if (last || (k % a.check_every == 0)) {
+        if constexpr (kBatch) {
+            // ---- per-slice stop tests: one warp per slice, fixed order ----
+            if (last || (k % a.check_every == 0)) {
+                for (int sl = gw; sl < a.ns; sl += nw_grid) {
+                    if (__ldcg(&a.sl_solve[sl].done)) continue;
+                    const double trr = warp_sum_range(a.rr_row, __ldg(a.sl_rows + sl), __ldg(a.sl_rows + sl + 1), lane);
+                    const double tpp = __ldcg(&a.sl_solve[sl].pp);
+                    const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
+                    if (lane == 0 && (last || rho <= a.tol)) {
+                        a.sl_solve[sl] = SliceSolve{k, 1, rho, trr, tpp};
+                        atomicAdd(a.ndone, 1);
+                    }
+                }
+            }
+            if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+            if (ld_volatile(a.ndone) >= a.ns) {
+                if (blockIdx.x == 0 && tid == 0) {
+                    a.result->iters = k;
+                    a.result->status = SPLITSART_OK;
+                    a.result->rho = 0.0;
+                    a.result->rr = 0.0;
+                    a.result->pp = 0.0;
+                }
+                return;
+            }
+        } else if (last || (k % a.check_every == 0)) {
+            // ---- stop test: every CTA sums the partials in the same order ----
             if (wib == 0) {
                 double t0, t1;
                 grid_totals(a.partials, gridDim.x, lane, t0, t1);
@@ -367,7 +443,11 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
                 }
                 b1 = warp_sum(b1, LPC);
                 b2 = warp_sum(b2, LPC);
-                if (sub == 0 && j >= 0) {
+                bool frozen = false;  // the slice of column j has stopped: keep its returned iterate
+                if constexpr (kBatch) {
+                    if (sub == 0 && j >= 0) frozen = __ldcg(&a.sl_solve[slice_index(a.sl_cols, a.ns, j)].done) != 0;
+                }
+                if (sub == 0 && j >= 0 && !frozen) {
                     const typename T::Norm2 ic = ldg(a.invC + j);
                     V2 f = ldcg(a.f12 + j);
                     if constexpr (T::kQuant) {
@@ -773,6 +853,12 @@ void fill_args(SartArgs<T>& a, splitsart_system* s, const void* p12, void* f12, 
     a.tile_entries = default_tile_entries<T>();
     a.direct_rows = 0;
     a.direct_cols = 0;
+    a.ns = s->ns;
+    a.sl_rows = s->sl_rows;
+    a.sl_cols = s->sl_cols;
+    a.sl_solve = s->sl_solve;
+    a.rr_row = s->rr_row;
+    a.ndone = s->ndone;
 }
 
 // Upper bound of one CTA's resident shared-memory bytes for a grid of G CTAs.
@@ -810,7 +896,8 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
     const int res_threads = (o.block_threads > 0 && o.block_threads <= 512) ? o.block_threads : 512;
     const long long res_avail = (long long)smem_optin - (long long)fa.sharedSizeBytes -
                                 (long long)ResidentBytes<T>::kThread * res_threads - 32;
-    const bool res_ok = s->Mh <= 65536 && s->Nh <= 65536 && resident_bound<T>(fs, nsm) <= res_avail;
+    const bool batch = s->ns > 1;
+    const bool res_ok = !batch && s->Mh <= 65536 && s->Nh <= 65536 && resident_bound<T>(fs, nsm) <= res_avail;
     if (o.kernel == 2 && !res_ok)
         return fail(SPLITSART_ERR_ARG, "solve: the system does not fit in shared memory (need %lld of %lld bytes per SM)",
                     resident_bound<T>(fs, nsm), res_avail);
@@ -827,7 +914,7 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
         smem_bytes = (int)dyn;
         grid = nsm;
     } else {
-        kern = (void*)sart_stream_kernel<T, LPC>;
+        kern = batch ? (void*)sart_stream_kernel<T, LPC, false, true> : (void*)sart_stream_kernel<T, LPC>;
         dyn = sizeof(typename T::Vec2) * (size_t)default_tile_entries<T>();
     }
     e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
@@ -846,6 +933,8 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
     if ((e = cudaMemsetAsync(s->ctl, 0, sizeof(LaunchCtl), st)) != cudaSuccess) return cuda_fail(e, "solve: memset");
     // A result the launch never writes (a timeout) reads back as iters = -1.
     if ((e = cudaMemsetAsync(s->result, 0xff, sizeof(SolveResultDev), st)) != cudaSuccess)
+        return cuda_fail(e, "solve: memset");
+    if (batch && (e = cudaMemsetAsync(s->ndone, 0, sizeof(int), st)) != cudaSuccess)
         return cuda_fail(e, "solve: memset");
     void* args_stream[] = {&a};
     void* args_res[] = {&a, &smem_bytes};

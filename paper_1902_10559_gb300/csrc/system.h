@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "host_common.h"
 
@@ -36,10 +37,33 @@ struct SolveResultDev {
 // Upper bound on grid-reduction partials (CTAs of one persistent launch).
 constexpr int kMaxCtas = 4096;
 
+// Where each slice of a system lives in the global index spaces. A system
+// built from one geometry has one slice. A batch concatenates several
+// independent slices into one block-diagonal folded system.
+struct SliceMap {
+    int ns;
+    const long long* rows;  // [ns+1] prefix of Mh_s: folded rows
+    const long long* cols;  // [ns+1] prefix of Nh_s: folded columns
+    const long long* M;     // [ns+1] prefix of M_s: full projection vectors
+    const long long* N;     // [ns+1] prefix of N_s: full images
+    const int* nx;          // [ns] 0 when the slice came from a CSR
+    const int* nz;          // [ns]
+};
+
+// Per-slice solve state of a batch launch.
+struct SliceSolve {
+    int iters;
+    int done;
+    double rho, rr, pp;
+};
+
 }  // namespace splitsart
 
 struct splitsart_system {
     int64_t M = 0, N = 0, Mh = 0, Nh = 0, nnz_half = 0;
+    int ns = 1;  // slices
+    std::vector<long long> h_rows, h_cols, h_M, h_N;  // host copies of the slice prefixes
+    std::vector<int> h_nx, h_nz;
     int dtype = 0;
     int nx = 0, nz = 0;
     int64_t S = -1;  // host copy, read lazily
@@ -75,6 +99,17 @@ struct splitsart_system {
     int32_t* nzc = nullptr;   // columns with entries (n_nzc)
     int32_t* nzcp = nullptr;  // cp of those columns, plus S at the end (n_nzc + 1)
 
+    // Slice map (device).
+    long long* sl_rows = nullptr;
+    long long* sl_cols = nullptr;
+    long long* sl_M = nullptr;
+    long long* sl_N = nullptr;
+    int* sl_nx = nullptr;
+    int* sl_nz = nullptr;
+    splitsart::SliceSolve* sl_solve = nullptr;  // [ns]
+    double* rr_row = nullptr;                   // [Mh] per-row residual^2 (batch solves)
+    int* ndone = nullptr;                       // slices finished (batch solves)
+
     // Scratch.
     int32_t* cnt = nullptr;          // max(Mh, Nh) + 1 counters
     int32_t* flags = nullptr;        // max(Mh, Nh) + 1 scan scratch
@@ -90,6 +125,9 @@ struct splitsart_system {
 };
 
 namespace splitsart {
+inline SliceMap slice_map(const splitsart_system* s) {
+    return SliceMap{s->ns, s->sl_rows, s->sl_cols, s->sl_M, s->sl_N, s->sl_nx, s->sl_nz};
+}
 // Defined in fold.cu.
 int run_fold(splitsart_system* s, cudaStream_t st);
 int run_fold_rhs(const splitsart_system* s, const void* p, void* p12, cudaStream_t st);

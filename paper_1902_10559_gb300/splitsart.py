@@ -35,7 +35,8 @@ class SystemInfo(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int64), ("N", ctypes.c_int64), ("Mh", ctypes.c_int64), ("Nh", ctypes.c_int64),
                 ("nnz_half", ctypes.c_int64), ("S", ctypes.c_int64), ("empty_rows", ctypes.c_int64),
                 ("exact_zeros", ctypes.c_int64), ("dtype", ctypes.c_int32), ("nx", ctypes.c_int32),
-                ("nz", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+                ("nz", ctypes.c_int32), ("device_bytes", ctypes.c_int64), ("nslices", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -68,6 +69,9 @@ _SIGS = {
     "splitsart_geometry_export": ([_P, _P, _P, _P], ctypes.c_int),
     "splitsart_geometry_destroy": ([_P], None),
     "splitsart_fold_system": ([_P, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "splitsart_fold_batch": ([ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "splitsart_system_slices": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "splitsart_solve_result_slices": ([_P, ctypes.POINTER(SolveInfo), ctypes.c_int], ctypes.c_int),
     "splitsart_refold": ([_P, _P], ctypes.c_int),
     "splitsart_system_info_get": ([_P, ctypes.POINTER(SystemInfo)], ctypes.c_int),
     "splitsart_system_export": ([_P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
@@ -181,13 +185,16 @@ def make_geometry_from_csr(M: int, N: int, row_ptr, col, val) -> Geometry:
 
 
 class System:
-    """Folded A1/A2 on the device. Wraps a ``splitsart_system`` handle."""
+    """Folded A1/A2 on the device, for one slice or a batch. Wraps a ``splitsart_system`` handle."""
 
-    def __init__(self, handle: int, dtype: int, geometry: Geometry):
+    def __init__(self, handle: int, dtype: int, geometry, geometries=None):
         self._h = ctypes.c_void_p(handle)
         self.dtype = dtype
         self.geometry = geometry
-        self.M, self.N = geometry.M, geometry.N
+        self.geometries = geometries if geometries is not None else [geometry]
+        self.nslices = len(self.geometries)
+        self.M = sum(g.M for g in self.geometries)
+        self.N = sum(g.N for g in self.geometries)
         self.Mh, self.Nh = self.M // 2, self.N // 2
 
     @property
@@ -240,6 +247,29 @@ def fold_system(geometry: Geometry, dtype: int = F32, stream=None) -> System:
     h = ctypes.c_void_p()
     _check(lib().splitsart_fold_system(geometry._h, dtype, _stream_ptr(stream), ctypes.byref(h)))
     return System(h.value, dtype, geometry)
+
+
+def fold_batch(geometries, dtype: int = F32, stream=None) -> System:
+    """Fold several independent slices into one block-diagonal batch system."""
+    arr = (_P * len(geometries))(*[g._h.value for g in geometries])
+    h = ctypes.c_void_p()
+    _check(lib().splitsart_fold_batch(arr, len(geometries), dtype, _stream_ptr(stream), ctypes.byref(h)))
+    return System(h.value, dtype, geometries[0], list(geometries))
+
+
+def system_slices(system: System) -> dict:
+    """Slice offsets (arrays of nslices + 1) in the full and folded index spaces."""
+    n = system.nslices + 1
+    out = {k: np.zeros(n, dtype=np.int64) for k in ("M", "N", "Mh", "Nh")}
+    _check(lib().splitsart_system_slices(system.handle, out["M"].ctypes.data, out["N"].ctypes.data,
+                                         out["Mh"].ctypes.data, out["Nh"].ctypes.data))
+    return out
+
+
+def solve_result_slices(system: System) -> list:
+    infos = (SolveInfo * system.nslices)()
+    _check(lib().splitsart_solve_result_slices(system.handle, infos, system.nslices))
+    return [{"iters": i.iters, "status": i.status, "rho": i.rho, "rr": i.rr, "pp": i.pp} for i in infos]
 
 
 def refold(system: System, stream=None) -> None:

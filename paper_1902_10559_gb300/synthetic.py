@@ -125,3 +125,44 @@ def noise_draws(M: int, config_id: int, stream: int = 1) -> np.ndarray:
 def apply_noise(p: np.ndarray, eps: np.ndarray, sigma: float) -> np.ndarray:
     """Apply the multiplicative noise: p (1 + sigma eps)."""
     return p * (1.0 + sigma * eps)
+
+
+def covering_detector_width(nx: int, nz: int, W: float, H: float, z0: float, K: int, gamma_deg: float,
+                            R: float, margin: float = 1.02) -> float:
+    """Return the smallest detector width D that covers the object's shadow from every source, times ``margin``.
+
+    The sources sit on the arc of the acquisition.
+    """
+    gam = math.radians(gamma_deg)
+    far = 0.0
+    for k in range(K):
+        th = gam * (2 * k + 1 - K) / (K - 1)
+        sx, sz = R * math.sin(th), R * math.cos(th)
+        for cx in (-W / 2, W / 2):
+            for cz in (z0, z0 + H):
+                far = max(far, abs(sx + (cx - sx) * sz / (sz - cz)))
+    return 2.0 * far * margin
+
+
+def batch_geometries(n_slices: int = 256, seed: int = 3, nx_choices=(256, 512, 768, 1024), nz_range=(64, 256),
+                     K_range=(16, 32)) -> list:
+    """Draw a batch of uneven slices with seeded sizes.
+
+    Each slice has:
+    - nx uniform in ``nx_choices``, nz uniform in ``nz_range`` and K uniform in
+      ``K_range`` (both integer and inclusive);
+    - nb = 2 nx detector bins;
+    - cells of 0.5 mm in x and 1 mm in z, so W = nx/2 mm and H = nz mm;
+    - z0 = 50 mm, sources on +/-25 deg at 600 mm;
+    - the smallest covering detector width.
+    """
+    rng = rng_for(seed, 0)
+    out = []
+    for _ in range(n_slices):
+        nx = int(rng.choice(nx_choices))
+        nz = int(rng.integers(nz_range[0], nz_range[1] + 1))
+        K = int(rng.integers(K_range[0], K_range[1] + 1))
+        W, H = 0.5 * nx, 1.0 * nz
+        D = covering_detector_width(nx, nz, W, H, 50.0, K, 25.0, 600.0)
+        out.append(Geometry(nx=nx, nz=nz, W=W, H=H, z0=50.0, K=K, gamma_deg=25.0, R=600.0, nb=2 * nx, D=D))
+    return out
