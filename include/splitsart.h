@@ -358,6 +358,29 @@ int splitsart_solve_static(int64_t Mh, int64_t Nh, const int32_t* rp_dev, const 
                            splitsart_solve_info* info_dev, void* stream);
 
 /*
+ * Solve one system for many right-hand sides at once, as a sparse matrix
+ * times a block of vectors.
+ * - Each right-hand side is an independent split-SART solve (the update and
+ *   the stopping test of splitsart_solve), with its own iteration count and
+ *   rho. The matrix is shared.
+ * - The whole folded system is kept in each CTA's shared memory, together
+ *   with rhs_per_cta right-hand sides (0 = library default, 4; allowed 1, 2,
+ *   4, 8, 16). Every matrix entry read serves all of them.
+ * - An iteration touches no global memory, so the launch needs no grid-wide
+ *   barrier.
+ * - The system must be a single slice small enough for shared memory.
+ *   Otherwise SPLITSART_ERR_ARG: use splitsart_solve per right-hand side.
+ * Arguments:
+ * - p12_dev: pair[nrhs][Mh], each right-hand side's folded p, contiguous.
+ * - f12_dev: pair[nrhs][Nh], in: f0, out: the results.
+ * - info_dev: device splitsart_solve_info[nrhs], written as each right-hand
+ *   side stops.
+ */
+int splitsart_solve_multi(splitsart_system* sys, int nrhs, const void* p12_dev, void* f12_dev,
+                          const splitsart_solve_opts* opts, int rhs_per_cta, splitsart_solve_info* info_dev,
+                          void* stream);
+
+/*
  * Per-slice results of the last solve of a batch system. info has at least
  * nslices entries. Synchronises like splitsart_solve_result. A single-slice
  * system reports its one result.

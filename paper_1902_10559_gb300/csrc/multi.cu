@@ -1,0 +1,320 @@
+// Many right-hand sides on one folded system: the split-SART iteration as a
+// sparse matrix times a block of vectors (SpMM).
+//
+// The method is SART on each split system (Section 1, reference [001];
+// Eqs. 3, 4). Every right-hand side is an independent solve with its own
+// stopping test; only the matrix is shared.
+//
+// Layout. The whole folded system (CSR, CSC, normalisers) is copied into each
+// CTA's shared memory once per launch. Each CTA owns RC right-hand sides, with
+// their p, u and f also in shared memory. An iteration therefore touches no
+// global memory, and the two phases are separated by CTA barriers only. The
+// launch needs no grid-wide synchronisation.
+//
+// SpMM. A warp takes one row (forward) or one column (back). Its 32 lanes are
+// split into RC groups of 32/RC lanes, one group per right-hand side. Every
+// matrix entry read from shared memory (a broadcast) is applied to all RC
+// right-hand sides.
+#include <cmath>
+#include <cstdio>
+
+#include "device_common.cuh"
+#include "system.h"
+
+namespace splitsart {
+
+namespace {
+
+template <class T>
+struct MultiArgs {
+    const int32_t* rp;
+    const int32_t* col;
+    const typename T::Pair* val;
+    const int32_t* cp;
+    const int32_t* row;
+    const typename T::Pair* valT;
+    const typename T::Norm2* invR;
+    const typename T::Norm2* invC;
+    const float2* scale;
+    const typename T::Vec2* p12;  // [nrhs][Mh]
+    typename T::Vec2* f12;        // [nrhs][Nh]
+    splitsart_solve_info* info;   // [nrhs]
+    int Mh, Nh, S, nrhs;
+    int max_iters, check_every;
+    double lambda, tol;
+};
+
+__device__ __forceinline__ size_t align16m(size_t x) { return (x + 15) & ~size_t(15); }
+
+template <class T, int RC>
+__global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
+    using Acc = typename T::Acc;
+    using V2 = typename T::Vec2;
+    using N2 = typename T::Norm2;
+    using Pair = typename T::Pair;
+    constexpr int L = 32 / RC;  // lanes per right-hand side
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_rr[16][RC], s_pp[16][RC];
+    __shared__ int s_done[RC], s_iters[RC], s_ndone;
+    __shared__ double s_rho[RC];
+
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nwarps = blockDim.x >> 5;
+    const int g = lane / L, sub = lane % L;       // right-hand side group and lane within it
+    const int r0 = blockIdx.x * RC;                // first right-hand side of this CTA
+    const int Mh = a.Mh, Nh = a.Nh, S = a.S;
+    const Acc lam = (Acc)a.lambda;
+
+    size_t off = 0;
+    int* s_rp = reinterpret_cast<int*>(smem + off);
+    off = align16m(off + 4 * (size_t)(Mh + 1));
+    int* s_col = reinterpret_cast<int*>(smem + off);
+    off = align16m(off + 4 * (size_t)S);
+    Pair* s_val = reinterpret_cast<Pair*>(smem + off);
+    off = align16m(off + sizeof(Pair) * (size_t)S);
+    int* s_cp = reinterpret_cast<int*>(smem + off);
+    off = align16m(off + 4 * (size_t)(Nh + 1));
+    int* s_row = reinterpret_cast<int*>(smem + off);
+    off = align16m(off + 4 * (size_t)S);
+    Pair* s_valT = reinterpret_cast<Pair*>(smem + off);
+    off = align16m(off + sizeof(Pair) * (size_t)S);
+    N2* s_ir = reinterpret_cast<N2*>(smem + off);
+    off = align16m(off + sizeof(N2) * (size_t)Mh);
+    N2* s_ic = reinterpret_cast<N2*>(smem + off);
+    off = align16m(off + sizeof(N2) * (size_t)Nh);
+    float2* s_sc = reinterpret_cast<float2*>(smem + off);
+    off = align16m(off + (T::kQuant ? sizeof(float2) * (size_t)Mh : 0));
+    V2* s_p = reinterpret_cast<V2*>(smem + off);  // [Mh][RC]
+    off = align16m(off + sizeof(V2) * (size_t)Mh * RC);
+    V2* s_u = reinterpret_cast<V2*>(smem + off);  // [Mh][RC]
+    off = align16m(off + sizeof(V2) * (size_t)Mh * RC);
+    V2* s_f = reinterpret_cast<V2*>(smem + off);  // [Nh][RC]
+
+    for (int i = tid; i <= Mh; i += blockDim.x) s_rp[i] = a.rp[i];
+    for (int j = tid; j <= Nh; j += blockDim.x) s_cp[j] = a.cp[j];
+    for (int e = tid; e < S; e += blockDim.x) {
+        s_col[e] = a.col[e];
+        s_val[e] = a.val[e];
+        s_row[e] = a.row[e];
+        s_valT[e] = a.valT[e];
+    }
+    for (int i = tid; i < Mh; i += blockDim.x) {
+        s_ir[i] = a.invR[i];
+        if constexpr (T::kQuant) s_sc[i] = a.scale[i];
+    }
+    for (int j = tid; j < Nh; j += blockDim.x) s_ic[j] = a.invC[j];
+    for (int t = tid; t < Mh * RC; t += blockDim.x) {
+        const int i = t / RC, r = t % RC;
+        s_p[t] = r0 + r < a.nrhs ? a.p12[(size_t)(r0 + r) * Mh + i] : V2{};
+    }
+    for (int t = tid; t < Nh * RC; t += blockDim.x) {
+        const int j = t / RC, r = t % RC;
+        s_f[t] = r0 + r < a.nrhs ? a.f12[(size_t)(r0 + r) * Nh + j] : V2{};
+    }
+    if (tid < RC) {
+        s_done[tid] = (r0 + tid >= a.nrhs);  // padding right-hand sides count as done
+        s_iters[tid] = -1;
+        s_rho[tid] = 0.0;
+    }
+    if (tid == 0) {
+        int n = 0;
+        for (int r = 0; r < RC; ++r) n += (r0 + r >= a.nrhs);
+        s_ndone = n;
+    }
+    __syncthreads();
+
+    for (int k = 0;; ++k) {
+        // ---- forward: one warp per row, RC groups of L lanes ----
+        double rr = 0.0, pp = 0.0;  // for right-hand side g, summed by the group's lane 0
+        for (int i = wib; i < Mh; i += nwarps) {
+            const int lo = s_rp[i], hi = s_rp[i + 1];
+            Acc s1 = 0, s2 = 0;
+            for (int e = lo + sub; e < hi; e += L) {
+                Acc a1, a2;
+                T::decode(s_val[e], a1, a2);
+                const V2 fv = s_f[s_col[e] * RC + g];
+                s1 += a1 * fv.x;
+                s2 += a2 * fv.y;
+            }
+            s1 = warp_sum(s1, L);
+            s2 = warp_sum(s2, L);
+            if (sub == 0) {
+                const V2 p = s_p[i * RC + g];
+                const N2 ir = s_ir[i];
+                V2 u;
+                Acc r1, r2;
+                if constexpr (T::kQuant) {
+                    const float2 sc = s_sc[i];
+                    r1 = p.x - s1 * sc.x;
+                    r2 = p.y - s2 * sc.y;
+                    u.x = (Acc)((double)r1 * ir.x * (double)sc.x);
+                    u.y = (Acc)((double)r2 * ir.y * (double)sc.y);
+                } else {
+                    r1 = p.x - s1;
+                    r2 = p.y - s2;
+                    u.x = r1 * ir.x;
+                    u.y = r2 * ir.y;
+                }
+                s_u[i * RC + g] = u;
+                rr += (double)r1 * (double)r1 + (double)r2 * (double)r2;
+                pp += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+            }
+        }
+        if (sub == 0) {
+            s_rr[wib][g] = rr;
+            s_pp[wib][g] = pp;
+        }
+        __syncthreads();
+        // ---- stop tests, one thread per right-hand side, fixed order ----
+        const bool last = k >= a.max_iters;
+        if (last || (k % a.check_every == 0)) {
+            if (tid < RC && !s_done[tid]) {
+                double t0 = 0.0, t1 = 0.0;
+                for (int w = 0; w < nwarps; ++w) {
+                    t0 += s_rr[w][tid];
+                    t1 += s_pp[w][tid];
+                }
+                const double rho = t1 > 0.0 ? sqrt(t0 / t1) : 0.0;
+                if (last || rho <= a.tol) {
+                    s_done[tid] = 1;
+                    s_iters[tid] = k;
+                    s_rho[tid] = rho;
+                    a.info[r0 + tid] = splitsart_solve_info{k, SPLITSART_OK, rho, t0, t1};
+                    atomicAdd(&s_ndone, 1);
+                }
+            }
+            __syncthreads();
+            if (s_ndone >= RC) break;
+        }
+        // ---- back-projection and update for the right-hand sides still running ----
+        for (int j = wib; j < Nh; j += nwarps) {
+            const int lo = s_cp[j], hi = s_cp[j + 1];
+            Acc b1 = 0, b2 = 0;
+            for (int e = lo + sub; e < hi; e += L) {
+                Acc a1, a2;
+                T::decode(s_valT[e], a1, a2);
+                const V2 uv = s_u[s_row[e] * RC + g];
+                b1 += a1 * uv.x;
+                b2 += a2 * uv.y;
+            }
+            b1 = warp_sum(b1, L);
+            b2 = warp_sum(b2, L);
+            if (sub == 0 && !s_done[g]) {
+                const N2 ic = s_ic[j];
+                V2 f = s_f[j * RC + g];
+                if constexpr (T::kQuant) {
+                    f.x += (Acc)((double)(lam * b1) * ic.x);
+                    f.y += (Acc)((double)(lam * b2) * ic.y);
+                } else {
+                    f.x += lam * b1 * ic.x;
+                    f.y += lam * b2 * ic.y;
+                }
+                s_f[j * RC + g] = f;
+            }
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < Nh * RC; t += blockDim.x) {
+        const int j = t / RC, r = t % RC;
+        if (r0 + r < a.nrhs) a.f12[(size_t)(r0 + r) * Nh + j] = s_f[t];
+    }
+}
+
+template <class T>
+size_t multi_smem_bytes(const splitsart_system* s, int S, int RC) {
+    auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
+    const size_t pb = sizeof(typename T::Pair), nb = sizeof(typename T::Norm2), vb = sizeof(typename T::Vec2);
+    return al(4 * (s->Mh + 1)) + al(4 * (size_t)S) + al(pb * S) + al(4 * (s->Nh + 1)) + al(4 * (size_t)S) +
+           al(pb * S) + al(nb * s->Mh) + al(nb * s->Nh) + (T::kQuant ? al(8 * s->Mh) : 0) + 2 * al(vb * s->Mh * RC) +
+           al(vb * s->Nh * RC);
+}
+
+template <class T, int RC>
+int launch_multi(splitsart_system* s, int S, int nrhs, const void* p12, void* f12, const splitsart_solve_opts& o,
+                 splitsart_solve_info* info, cudaStream_t st) {
+    auto kern = sart_multi_kernel<T, RC>;
+    const size_t dyn = multi_smem_bytes<T>(s, S, RC);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)kern);
+    if (e != cudaSuccess) return cuda_fail(e, "solve_multi: kernel attributes");
+    if (dyn + fa.sharedSizeBytes > (size_t)optin)
+        return fail(SPLITSART_ERR_ARG, "solve_multi: the system and %d right-hand sides need %zu bytes of shared memory "
+                                       "per CTA (limit %d); use fewer per CTA or splitsart_solve",
+                    RC, dyn + fa.sharedSizeBytes, optin);
+    e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return cuda_fail(e, "solve_multi: shared memory attribute");
+    MultiArgs<T> a;
+    a.rp = s->rp;
+    a.col = s->col;
+    a.val = (const typename T::Pair*)s->val;
+    a.cp = s->cp;
+    a.row = s->row;
+    a.valT = (const typename T::Pair*)s->valT;
+    a.invR = (const typename T::Norm2*)s->invR;
+    a.invC = (const typename T::Norm2*)s->invC;
+    a.scale = s->scale;
+    a.p12 = (const typename T::Vec2*)p12;
+    a.f12 = (typename T::Vec2*)f12;
+    a.info = info;
+    a.Mh = (int)s->Mh;
+    a.Nh = (int)s->Nh;
+    a.S = S;
+    a.nrhs = nrhs;
+    a.max_iters = o.max_iters;
+    a.check_every = o.check_every > 0 ? o.check_every : 1;
+    a.lambda = o.lambda;
+    a.tol = o.tol;
+    const int threads = o.block_threads > 0 ? o.block_threads : 512;
+    if (threads % 32 || threads > 512 || threads < 32)
+        return fail(SPLITSART_ERR_ARG, "solve_multi: block_threads must be a multiple of 32 in [32, 512]");
+    const int grid = (nrhs + RC - 1) / RC;
+    kern<<<grid, threads, dyn, st>>>(a);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? SPLITSART_OK : cuda_fail(e, "solve_multi: launch");
+}
+
+template <class T>
+int multi_typed(splitsart_system* s, int S, int nrhs, int rc, const void* p12, void* f12,
+                const splitsart_solve_opts& o, splitsart_solve_info* info, cudaStream_t st) {
+    switch (rc) {
+        case 1: return launch_multi<T, 1>(s, S, nrhs, p12, f12, o, info, st);
+        case 2: return launch_multi<T, 2>(s, S, nrhs, p12, f12, o, info, st);
+        case 4: return launch_multi<T, 4>(s, S, nrhs, p12, f12, o, info, st);
+        case 8: return launch_multi<T, 8>(s, S, nrhs, p12, f12, o, info, st);
+        case 16: return launch_multi<T, 16>(s, S, nrhs, p12, f12, o, info, st);
+    }
+    return fail(SPLITSART_ERR_ARG, "solve_multi: rhs_per_cta must be 1, 2, 4, 8 or 16");
+}
+
+}  // namespace
+
+}  // namespace splitsart
+
+using namespace splitsart;
+
+extern "C" int splitsart_solve_multi(splitsart_system* s, int nrhs, const void* p12_dev, void* f12_dev,
+                                     const splitsart_solve_opts* o, int rhs_per_cta, splitsart_solve_info* info_dev,
+                                     void* stream) {
+    if (!s || !o || !p12_dev || !f12_dev || !info_dev) return fail(SPLITSART_ERR_ARG, "solve_multi: NULL argument");
+    if (nrhs < 1) return fail(SPLITSART_ERR_ARG, "solve_multi: nrhs must be >= 1");
+    if (s->ns != 1) return fail(SPLITSART_ERR_ARG, "solve_multi: needs a single-slice system");
+    if (o->max_iters < 0 || o->max_iters > 500000) return fail(SPLITSART_ERR_ARG, "solve_multi: bad max_iters");
+    if (!(o->lambda > 0.0) || !std::isfinite(o->lambda)) return fail(SPLITSART_ERR_ARG, "solve_multi: lambda must be > 0");
+    if (!(o->tol >= 0.0) || o->check_every < 0) return fail(SPLITSART_ERR_ARG, "solve_multi: bad tol or check_every");
+    FoldStats fs;
+    int rc = system_host_stats(s, &fs);
+    if (rc) return rc;
+    const int per = rhs_per_cta > 0 ? rhs_per_cta : 4;
+    cudaStream_t st = (cudaStream_t)stream;
+    s->last = st;
+    const int S = (int)fs.S;
+    switch (s->dtype) {
+        case SPLITSART_F64: return multi_typed<TF64>(s, S, nrhs, per, p12_dev, f12_dev, *o, info_dev, st);
+        case SPLITSART_F32: return multi_typed<TF32>(s, S, nrhs, per, p12_dev, f12_dev, *o, info_dev, st);
+        case SPLITSART_BF16: return multi_typed<TBF16>(s, S, nrhs, per, p12_dev, f12_dev, *o, info_dev, st);
+        case SPLITSART_F16: return multi_typed<TF16>(s, S, nrhs, per, p12_dev, f12_dev, *o, info_dev, st);
+    }
+    return fail(SPLITSART_ERR_ARG, "solve_multi: unknown dtype");
+}

@@ -72,6 +72,7 @@ _SIGS = {
     "splitsart_fold_batch": ([ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "splitsart_system_slices": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "splitsart_solve_result_slices": ([_P, ctypes.POINTER(SolveInfo), ctypes.c_int], ctypes.c_int),
+    "splitsart_solve_multi": ([_P, ctypes.c_int, _P, _P, ctypes.POINTER(SolveOpts), ctypes.c_int, _P, _P], ctypes.c_int),
     "splitsart_refold": ([_P, _P], ctypes.c_int),
     "splitsart_system_info_get": ([_P, ctypes.POINTER(SystemInfo)], ctypes.c_int),
     "splitsart_system_export": ([_P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
@@ -343,6 +344,27 @@ def solve_static(Mh: int, Nh: int, rp, col, val, cp, row, valT, invR, invC, p12,
         _dev_ptr(invR, 2 * Mh, f32, "invR"), _dev_ptr(invC, 2 * Nh, f32, "invC"),
         _dev_ptr(p12, 2 * Mh, f32, "p12"), _dev_ptr(f12, 2 * Nh, f32, "f12"), ctypes.byref(opts), info.data_ptr(),
         _stream_ptr(stream)))
+
+
+def solve_multi(system: System, p12, f12, opts: SolveOpts, info, rhs_per_cta: int = 0, stream=None) -> None:
+    """Solve nrhs right-hand sides at once. p12: [nrhs, Mh, 2], f12: [nrhs, Nh, 2] (in: f0, out: results).
+
+    ``info`` is a CUDA uint8 tensor of nrhs * sizeof(SolveInfo) bytes; decode it with ``read_infos``.
+    """
+    import torch
+    vt = system.vec_dtype
+    nrhs = p12.shape[0]
+    if info.dtype != torch.uint8 or not info.is_cuda or info.numel() < nrhs * ctypes.sizeof(SolveInfo):
+        raise ValueError("info: expected a CUDA uint8 tensor of nrhs * sizeof(SolveInfo) bytes")
+    _check(lib().splitsart_solve_multi(system.handle, nrhs, _dev_ptr(p12, 2 * system.Mh * nrhs, vt, "p12"),
+                                       _dev_ptr(f12, 2 * system.Nh * nrhs, vt, "f12"), ctypes.byref(opts),
+                                       rhs_per_cta, info.data_ptr(), _stream_ptr(stream)))
+
+
+def read_infos(info, n: int) -> list:
+    raw = bytes(info[: n * ctypes.sizeof(SolveInfo)].cpu().numpy().tobytes())
+    arr = (SolveInfo * n).from_buffer_copy(raw)
+    return [{"iters": s.iters, "status": s.status, "rho": s.rho, "rr": s.rr, "pp": s.pp} for s in arr]
 
 
 def read_info(info) -> dict:

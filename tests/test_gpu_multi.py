@@ -1,0 +1,79 @@
+"""Many right-hand sides on one system (SpMM form), on the GPU.
+
+64 right-hand sides share the tiny slice's geometry. Every right-hand side
+must match the FP64 oracle and stop on its own.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import geometry as ogeo
+from oracle import sart as osart
+from oracle import split as osplit
+from paper_1902_10559_gb300.synthetic import TINY, random_phantom
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ss():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1902_10559_gb300 import build, splitsart
+    build.build()
+    splitsart.lib()
+    return splitsart
+
+
+@pytest.fixture(scope="module")
+def case():
+    g = TINY
+    A = ogeo.mirrored_system_matrix(g)
+    A1, A2 = osplit.fold_matrix(A)
+    fs = [ogeo.image_to_snake(g, random_phantom(g, 40, 8, stream=r)) for r in range(64)]
+    ps = [A @ f for f in fs]
+    return g, A1, A2, ps
+
+
+def run(ss, system, ps, iters, lam, tol=0.0, rc=0):
+    vt = system.vec_dtype
+    n = len(ps)
+    p = torch.as_tensor(np.stack(ps), dtype=vt, device="cuda")
+    p12 = torch.empty(n, system.Mh, 2, dtype=vt, device="cuda")
+    for r in range(n):
+        ss.fold_rhs(system, p[r].contiguous(), p12[r])
+    f12 = torch.zeros(n, system.Nh, 2, dtype=vt, device="cuda")
+    info = torch.zeros(n * ctypes.sizeof(ss.SolveInfo), dtype=torch.uint8, device="cuda")
+    ss.solve_multi(system, p12, f12, ss.solve_opts(iters, lam, tol), info, rhs_per_cta=rc)
+    torch.cuda.synchronize()
+    return ss.read_infos(info, n), f12.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("dt,tol,rc", [("f64", 1e-10, 4), ("f32", 1e-4, 1), ("f32", 1e-4, 8), ("bf16", 2e-3, 16)])
+def test_multi_rhs_matches_oracle(ss, case, dt, tol, rc):
+    g, A1, A2, ps = case
+    system = ss.fold_system(ss.make_geometry(g), ss.DTYPE_NAMES[dt])
+    infos, f12 = run(ss, system, ps, 100, 1.0, rc=rc)
+    for r in (0, 1, 17, 63):
+        p1, p2 = osplit.fold_rhs(ps[r])
+        ref = osart.split_sart(A1, A2, p1, p2, 1.0, 100)
+        f_ref = osplit.recombine(ref["f1"], ref["f2"])
+        f = osplit.recombine(f12[r, :, 0], f12[r, :, 1])
+        assert infos[r]["iters"] == 100 and infos[r]["status"] == 0
+        assert np.linalg.norm(f - f_ref) / np.linalg.norm(f_ref) <= tol, r
+
+
+def test_multi_rhs_stop_individually(ss, case):
+    g, A1, A2, ps = case
+    system = ss.fold_system(ss.make_geometry(g), ss.F64)
+    hists = []
+    for r in range(8):
+        p1, p2 = osplit.fold_rhs(ps[r])
+        hists.append(osart.split_sart(A1, A2, p1, p2, 1.0, 80, record=True)["rho_hist"])
+    tol = float(np.median([h[30] for h in hists]))
+    expect = [next((k for k, x in enumerate(h) if x <= tol), 80) for h in hists]
+    assert len(set(expect)) > 1
+    infos, f12 = run(ss, system, ps[:8], 80, 1.0, tol=tol, rc=4)
+    assert [i["iters"] for i in infos] == expect
