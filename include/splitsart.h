@@ -273,7 +273,7 @@ typedef struct splitsart_solve_opts {
     int32_t kernel;        /* 0 = choose, 1 = stream the matrix from memory, 2 = keep it in shared memory */
     double timeout_ms;     /* limit of each grid-barrier wait; 0 = default (2000 ms) */
     int32_t inject_barrier_fault; /* test hook: the barrier also waits for a CTA that never comes */
-    int32_t reserved1;
+    int32_t tile_entries;  /* streaming kernel: entries staged per tile, 0 = default; multiple of 1024 in [1024, 16384] */
 } splitsart_solve_opts;
 
 /*

@@ -850,7 +850,7 @@ void fill_args(SartArgs<T>& a, splitsart_system* s, const void* p12, void* f12, 
     const double tms = o.timeout_ms > 0 ? o.timeout_ms : 2000.0;
     a.timeout_ns = (unsigned long long)(tms * 1e6);
     a.expected = grid + (o.inject_barrier_fault ? 1u : 0u);
-    a.tile_entries = default_tile_entries<T>();
+    a.tile_entries = o.tile_entries > 0 ? o.tile_entries : default_tile_entries<T>();
     a.direct_rows = 0;
     a.direct_cols = 0;
     a.ns = s->ns;
@@ -915,7 +915,13 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
         grid = nsm;
     } else {
         kern = batch ? (void*)sart_stream_kernel<T, LPC, false, true> : (void*)sart_stream_kernel<T, LPC>;
-        dyn = sizeof(typename T::Vec2) * (size_t)default_tile_entries<T>();
+        dyn = sizeof(typename T::Vec2) * (size_t)(o.tile_entries > 0 ? o.tile_entries : default_tile_entries<T>());
+    }
+    if (!use_res) {
+        cudaFuncAttributes sa{};
+        if ((e = cudaFuncGetAttributes(&sa, (const void*)kern)) != cudaSuccess) return cuda_fail(e, "solve: attributes");
+        if (dyn + sa.sharedSizeBytes > (size_t)smem_optin)
+            return fail(SPLITSART_ERR_ARG, "solve: tile_entries too large for shared memory (%zu bytes)", dyn);
     }
     e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return cuda_fail(e, "solve: shared memory attribute");
