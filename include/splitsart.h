@@ -387,6 +387,61 @@ int splitsart_solve_multi(splitsart_system* sys, int nrhs, const void* p12_dev, 
  */
 int splitsart_solve_result_slices(splitsart_system* sys, splitsart_solve_info* info, int n);
 
+/*
+ * ---- Learned warm start ----
+ * The paper has no network. This is a small residual CNN that maps an early
+ * split-SART image to an initial guess for the solve. The guess is folded
+ * into (f1, f2) with splitsart_fold_image, as in the proof of Theorem 1, and
+ * the solve continues from it.
+ *
+ * Network, on images [B][nz][nx] (row r from the bottom, column c from the
+ * left, as SPLITSART_LAYOUT_IMAGE):
+ *     a1 = relu(conv(x, W1) + b1)     1 -> 32 channels
+ *     a2 = relu(conv(a1, W2) + b2)   32 -> 32
+ *     a3 = relu(conv(a2, W3) + b3)   32 -> 32
+ *     y  = x + conv(a3, W4) + b4     32 -> 1
+ * conv is a 3x3 cross-correlation with zero padding 1. Tap (dy, dx) reads
+ * pixel (r + dy - 1, c + dx - 1), and weights are [out][in][3][3].
+ * Parameters are one float vector of 19105 values, in the order W1, b1, W2,
+ * b2, W3, b3, W4, b4.
+ * Training minimises mean((y - t)^2) with Adam.
+ */
+typedef struct splitsart_cnn splitsart_cnn;
+
+/* Create the network for nz x nx images and batches up to max_batch, from
+ * initial parameters (host, 19105 floats). Device memory is allocated here.
+ * nx <= 256. */
+int splitsart_cnn_create(int nz, int nx, int max_batch, const float* params_host, splitsart_cnn** out);
+void splitsart_cnn_destroy(splitsart_cnn* cnn);
+
+/* Arithmetic of the two 32 -> 32 layers:
+ * - 0: FP32 on the CUDA cores (default);
+ * - 1: BF16 tcgen05 tensor-core MMAs with FP32 accumulation in tensor
+ *   memory (needs nx = 32 and nz*nx a multiple of 128).
+ * Layers 1 and 4, the weight gradients and Adam are FP32 in both modes. */
+int splitsart_cnn_set_mode(splitsart_cnn* cnn, int mode);
+
+/* Copy the parameters (and, if moments_host is non-NULL, the Adam moments
+ * m then v: 2 x 19105 floats) to the host. Synchronising. */
+int splitsart_cnn_params(splitsart_cnn* cnn, float* params_host, float* moments_host);
+
+/* Replace the parameters. moments_host may be NULL (then zeroed). step is
+ * the Adam step count already taken. Together with splitsart_cnn_params this
+ * gives checkpoint and resume. Synchronising. */
+int splitsart_cnn_set_params(splitsart_cnn* cnn, const float* params_host, const float* moments_host, int step);
+
+/* Inference: y_dev[B][nz][nx] = net(x_dev[B][nz][nx]). */
+int splitsart_cnn_forward(splitsart_cnn* cnn, const float* x_dev, int B, float* y_dev, void* stream);
+
+/* Loss and gradient without an update. loss_dev (1 float) and grad_dev (19105 floats) may each be NULL. */
+int splitsart_cnn_loss_grad(splitsart_cnn* cnn, const float* x_dev, const float* t_dev, int B, float* loss_dev,
+                            float* grad_dev, void* stream);
+
+/* One Adam step on the batch (x_dev, t_dev). loss_dev (1 float, may be NULL)
+ * receives the batch loss before the update. */
+int splitsart_cnn_train_step(splitsart_cnn* cnn, const float* x_dev, const float* t_dev, int B, double lr, double beta1,
+                             double beta2, double eps, float* loss_dev, void* stream);
+
 /* Copy the thread's last error message into buf (truncated, NUL-terminated). Returns its full length. */
 int splitsart_last_error(char* buf, size_t len);
 

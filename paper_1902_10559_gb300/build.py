@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "libsplitsart.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["api.cu", "fold.cu", "sart.cu", "multi.cu"]
+CU_SOURCES = ["api.cu", "fold.cu", "sart.cu", "multi.cu", "cnn.cu", "cnn_mma.cu"]
 CPP_SOURCES = ["geometry.cpp"]
 
 

@@ -86,6 +86,15 @@ _SIGS = {
     "splitsart_solve_result": ([_P, ctypes.POINTER(SolveInfo)], ctypes.c_int),
     "splitsart_solve_static": ([ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                 ctypes.POINTER(SolveOpts), _P, _P], ctypes.c_int),
+    "splitsart_cnn_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "splitsart_cnn_destroy": ([_P], None),
+    "splitsart_cnn_set_mode": ([_P, ctypes.c_int], ctypes.c_int),
+    "splitsart_cnn_params": ([_P, _P, _P], ctypes.c_int),
+    "splitsart_cnn_set_params": ([_P, _P, _P, ctypes.c_int], ctypes.c_int),
+    "splitsart_cnn_forward": ([_P, _P, ctypes.c_int, _P, _P], ctypes.c_int),
+    "splitsart_cnn_loss_grad": ([_P, _P, _P, ctypes.c_int, _P, _P, _P], ctypes.c_int),
+    "splitsart_cnn_train_step": ([_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, _P, _P], ctypes.c_int),
     "splitsart_last_error": ([ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
     "splitsart_version": ([], ctypes.c_char_p),
 }
@@ -372,6 +381,61 @@ def read_info(info) -> dict:
     raw = bytes(info[: ctypes.sizeof(SolveInfo)].cpu().numpy().tobytes())
     s = SolveInfo.from_buffer_copy(raw)
     return {"iters": s.iters, "status": s.status, "rho": s.rho, "rr": s.rr, "pp": s.pp}
+
+
+CNN_PARAMS = 19105
+
+
+class Cnn:
+    """The warm-start network. Wraps a ``splitsart_cnn`` handle; images are CUDA float32 [B, nz, nx]."""
+
+    def __init__(self, nz: int, nx: int, max_batch: int, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != CNN_PARAMS:
+            raise ValueError(f"expected {CNN_PARAMS} parameters")
+        h = ctypes.c_void_p()
+        _check(lib().splitsart_cnn_create(nz, nx, max_batch, p.ctypes.data, ctypes.byref(h)))
+        self._h = h
+        self.nz, self.nx, self.max_batch = nz, nx, max_batch
+
+    def _img(self, t, B, name):
+        import torch
+        return _dev_ptr(t, B * self.nz * self.nx, torch.float32, name)
+
+    def set_mode(self, mode: int) -> None:
+        _check(lib().splitsart_cnn_set_mode(self._h, mode))
+
+    def params(self, moments: bool = False):
+        p = np.zeros(CNN_PARAMS, dtype=np.float32)
+        mv = np.zeros(2 * CNN_PARAMS, dtype=np.float32) if moments else None
+        _check(lib().splitsart_cnn_params(self._h, p.ctypes.data, mv.ctypes.data if moments else None))
+        return (p, mv[:CNN_PARAMS], mv[CNN_PARAMS:]) if moments else p
+
+    def set_params(self, params, m=None, v=None, step: int = 0) -> None:
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        mv = None if m is None else np.ascontiguousarray(np.concatenate([m, v]), dtype=np.float32)
+        _check(lib().splitsart_cnn_set_params(self._h, p.ctypes.data, None if mv is None else mv.ctypes.data, step))
+
+    def forward(self, x, y, stream=None) -> None:
+        B = x.shape[0]
+        _check(lib().splitsart_cnn_forward(self._h, self._img(x, B, "x"), B, self._img(y, B, "y"), _stream_ptr(stream)))
+
+    def loss_grad(self, x, t, loss=None, grad=None, stream=None) -> None:
+        B = x.shape[0]
+        _check(lib().splitsart_cnn_loss_grad(self._h, self._img(x, B, "x"), self._img(t, B, "t"), B,
+                                             None if loss is None else loss.data_ptr(),
+                                             None if grad is None else grad.data_ptr(), _stream_ptr(stream)))
+
+    def train_step(self, x, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, loss=None, stream=None) -> None:
+        B = x.shape[0]
+        _check(lib().splitsart_cnn_train_step(self._h, self._img(x, B, "x"), self._img(t, B, "t"), B, lr, beta1,
+                                              beta2, eps, None if loss is None else loss.data_ptr(),
+                                              _stream_ptr(stream)))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.splitsart_cnn_destroy(self._h)
+            self._h = None
 
 
 def version() -> str:

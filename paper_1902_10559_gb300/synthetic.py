@@ -166,3 +166,22 @@ def batch_geometries(n_slices: int = 256, seed: int = 3, nx_choices=(256, 512, 7
         D = covering_detector_width(nx, nz, W, H, 50.0, K, 25.0, 600.0)
         out.append(Geometry(nx=nx, nz=nz, W=W, H=H, z0=50.0, K=K, gamma_deg=25.0, R=600.0, nb=2 * nx, D=D))
     return out
+
+
+def cnn_initial_params(seed: int = 5, channels: int = 32, out_scale: float = 0.1) -> np.ndarray:
+    """Seeded initial parameters of the warm-start network (flat float32 vector).
+
+    - The order is W1, b1, W2, b2, W3, b3, W4, b4, with weights [out][in][3][3].
+    - Weights are He-normal: N(0, 2 / fan_in).
+    - The last layer is scaled by ``out_scale``, so the untrained network is
+      close to the identity through its residual path.
+    - Biases start at zero.
+    """
+    rng = rng_for(seed, 7)
+    C = channels
+    parts = []
+    for cin, cout, scale in ((1, C, 1.0), (C, C, 1.0), (C, C, 1.0), (C, 1, out_scale)):
+        fan_in = cin * 9
+        parts.append(rng.standard_normal(cout * cin * 9) * math.sqrt(2.0 / fan_in) * scale)
+        parts.append(np.zeros(cout))
+    return np.concatenate(parts).astype(np.float32)
