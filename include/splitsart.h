@@ -381,6 +381,18 @@ int splitsart_solve_multi(splitsart_system* sys, int nrhs, const void* p12_dev, 
                           void* stream);
 
 /*
+ * Fallback rule of the warm start, per right-hand side r of a multi solve:
+ * if info_warm[r].rho < info_base[r].rho, f12_dev[r] := f12_warm_dev[r];
+ * otherwise f12_dev[r] (the base start) is kept. The rho values come from
+ * splitsart_solve_multi runs with max_iters = 0 (warm) and the early solve
+ * (base). picked_dev[r] (optional) receives 1 where the warm start was kept.
+ * f12 arrays are pair[nrhs][Nh] and info arrays device splitsart_solve_info[nrhs].
+ */
+int splitsart_pick_start(const splitsart_system* sys, int nrhs, const void* f12_warm_dev,
+                         const splitsart_solve_info* info_warm_dev, const splitsart_solve_info* info_base_dev,
+                         void* f12_dev, int* picked_dev, void* stream);
+
+/*
  * Per-slice results of the last solve of a batch system. info has at least
  * nslices entries. Synchronises like splitsart_solve_result. A single-slice
  * system reports its one result.

@@ -46,20 +46,24 @@ struct MultiArgs {
 
 __device__ __forceinline__ size_t align16m(size_t x) { return (x + 15) & ~size_t(15); }
 
-template <class T, int RC>
+// RC right-hand sides per CTA; RPW rows (or columns) per warp at a time; the
+// 32 lanes split into RPW x RC groups of LPR = 32 / (RPW RC) lanes.
+template <class T, int RC, int RPW>
 __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
     using Acc = typename T::Acc;
     using V2 = typename T::Vec2;
     using N2 = typename T::Norm2;
     using Pair = typename T::Pair;
-    constexpr int L = 32 / RC;  // lanes per right-hand side
+    constexpr int LPR = 32 / (RC * RPW);  // lanes per (row, right-hand side)
+    static_assert(LPR >= 1, "too many groups per warp");
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double s_rr[16][RC], s_pp[16][RC];
-    __shared__ int s_done[RC], s_iters[RC], s_ndone;
-    __shared__ double s_rho[RC];
+    __shared__ double s_rr[16][RPW][RC];
+    __shared__ double s_pp[RC];
+    __shared__ int s_done[RC], s_ndone;
 
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nwarps = blockDim.x >> 5;
-    const int g = lane / L, sub = lane % L;       // right-hand side group and lane within it
+    const int grp = lane / LPR, sub = lane % LPR;
+    const int g = grp % RC, rw = grp / RC;        // right-hand side and row slot of this lane group
     const int r0 = blockIdx.x * RC;                // first right-hand side of this CTA
     const int Mh = a.Mh, Nh = a.Nh, S = a.S;
     const Acc lam = (Acc)a.lambda;
@@ -110,10 +114,16 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
         const int j = t / RC, r = t % RC;
         s_f[t] = r0 + r < a.nrhs ? a.f12[(size_t)(r0 + r) * Nh + j] : V2{};
     }
+    __syncthreads();
     if (tid < RC) {
+        // ||p||^2 of each right-hand side, once, in a fixed order.
+        double t1 = 0.0;
+        for (int i = 0; i < Mh; ++i) {
+            const V2 p = s_p[i * RC + tid];
+            t1 += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+        }
+        s_pp[tid] = t1;
         s_done[tid] = (r0 + tid >= a.nrhs);  // padding right-hand sides count as done
-        s_iters[tid] = -1;
-        s_rho[tid] = 0.0;
     }
     if (tid == 0) {
         int n = 0;
@@ -123,21 +133,24 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
     __syncthreads();
 
     for (int k = 0;; ++k) {
-        // ---- forward: one warp per row, RC groups of L lanes ----
-        double rr = 0.0, pp = 0.0;  // for right-hand side g, summed by the group's lane 0
-        for (int i = wib; i < Mh; i += nwarps) {
-            const int lo = s_rp[i], hi = s_rp[i + 1];
+        // ---- forward: RPW rows per warp, one lane group per (row, right-hand side) ----
+        double rrd = 0.0;  // this lane group's ||r||^2 over its rows, FP64
+        for (int i0 = wib * RPW; i0 < Mh; i0 += nwarps * RPW) {
+            const int i = i0 + rw;
             Acc s1 = 0, s2 = 0;
-            for (int e = lo + sub; e < hi; e += L) {
-                Acc a1, a2;
-                T::decode(s_val[e], a1, a2);
-                const V2 fv = s_f[s_col[e] * RC + g];
-                s1 += a1 * fv.x;
-                s2 += a2 * fv.y;
+            if (i < Mh) {
+                const int lo = s_rp[i], hi = s_rp[i + 1];
+                for (int e = lo + sub; e < hi; e += LPR) {
+                    Acc a1, a2;
+                    T::decode(s_val[e], a1, a2);
+                    const V2 fv = s_f[s_col[e] * RC + g];
+                    s1 += a1 * fv.x;
+                    s2 += a2 * fv.y;
+                }
             }
-            s1 = warp_sum(s1, L);
-            s2 = warp_sum(s2, L);
-            if (sub == 0) {
+            s1 = warp_sum(s1, LPR);
+            s2 = warp_sum(s2, LPR);
+            if (sub == 0 && i < Mh) {
                 const V2 p = s_p[i * RC + g];
                 const N2 ir = s_ir[i];
                 V2 u;
@@ -155,29 +168,22 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
                     u.y = r2 * ir.y;
                 }
                 s_u[i * RC + g] = u;
-                rr += (double)r1 * (double)r1 + (double)r2 * (double)r2;
-                pp += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+                rrd += (double)r1 * (double)r1 + (double)r2 * (double)r2;
             }
         }
-        if (sub == 0) {
-            s_rr[wib][g] = rr;
-            s_pp[wib][g] = pp;
-        }
+        if (sub == 0) s_rr[wib][rw][g] = rrd;
         __syncthreads();
         // ---- stop tests, one thread per right-hand side, fixed order ----
         const bool last = k >= a.max_iters;
         if (last || (k % a.check_every == 0)) {
             if (tid < RC && !s_done[tid]) {
-                double t0 = 0.0, t1 = 0.0;
-                for (int w = 0; w < nwarps; ++w) {
-                    t0 += s_rr[w][tid];
-                    t1 += s_pp[w][tid];
-                }
+                double t0 = 0.0;
+                for (int w = 0; w < nwarps; ++w)
+                    for (int q = 0; q < RPW; ++q) t0 += s_rr[w][q][tid];
+                const double t1 = s_pp[tid];
                 const double rho = t1 > 0.0 ? sqrt(t0 / t1) : 0.0;
                 if (last || rho <= a.tol) {
                     s_done[tid] = 1;
-                    s_iters[tid] = k;
-                    s_rho[tid] = rho;
                     a.info[r0 + tid] = splitsart_solve_info{k, SPLITSART_OK, rho, t0, t1};
                     atomicAdd(&s_ndone, 1);
                 }
@@ -186,19 +192,22 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
             if (s_ndone >= RC) break;
         }
         // ---- back-projection and update for the right-hand sides still running ----
-        for (int j = wib; j < Nh; j += nwarps) {
-            const int lo = s_cp[j], hi = s_cp[j + 1];
+        for (int j0 = wib * RPW; j0 < Nh; j0 += nwarps * RPW) {
+            const int j = j0 + rw;
             Acc b1 = 0, b2 = 0;
-            for (int e = lo + sub; e < hi; e += L) {
-                Acc a1, a2;
-                T::decode(s_valT[e], a1, a2);
-                const V2 uv = s_u[s_row[e] * RC + g];
-                b1 += a1 * uv.x;
-                b2 += a2 * uv.y;
+            if (j < Nh) {
+                const int lo = s_cp[j], hi = s_cp[j + 1];
+                for (int e = lo + sub; e < hi; e += LPR) {
+                    Acc a1, a2;
+                    T::decode(s_valT[e], a1, a2);
+                    const V2 uv = s_u[s_row[e] * RC + g];
+                    b1 += a1 * uv.x;
+                    b2 += a2 * uv.y;
+                }
             }
-            b1 = warp_sum(b1, L);
-            b2 = warp_sum(b2, L);
-            if (sub == 0 && !s_done[g]) {
+            b1 = warp_sum(b1, LPR);
+            b2 = warp_sum(b2, LPR);
+            if (sub == 0 && j < Nh && !s_done[g]) {
                 const N2 ic = s_ic[j];
                 V2 f = s_f[j * RC + g];
                 if constexpr (T::kQuant) {
@@ -231,7 +240,10 @@ size_t multi_smem_bytes(const splitsart_system* s, int S, int RC) {
 template <class T, int RC>
 int launch_multi(splitsart_system* s, int S, int nrhs, const void* p12, void* f12, const splitsart_solve_opts& o,
                  splitsart_solve_info* info, cudaStream_t st) {
-    auto kern = sart_multi_kernel<T, RC>;
+    // Four lane groups per warp: up to 8 lanes per (row, right-hand side), about one
+    // entry each for a slice whose rows hold tens of entries.
+    constexpr int RPW = RC >= 4 ? 1 : 4 / RC;
+    auto kern = sart_multi_kernel<T, RC, RPW>;
     const size_t dyn = multi_smem_bytes<T>(s, S, RC);
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
@@ -288,11 +300,43 @@ int multi_typed(splitsart_system* s, int S, int nrhs, int rc, const void* p12, v
     return fail(SPLITSART_ERR_ARG, "solve_multi: rhs_per_cta must be 1, 2, 4, 8 or 16");
 }
 
+// Per right-hand side: keep the warm start only if its residual is lower.
+template <class V2>
+__global__ void pick_start_kernel(int nrhs, long long Nh, const V2* __restrict__ warm,
+                                  const splitsart_solve_info* __restrict__ iw, const splitsart_solve_info* __restrict__ ib,
+                                  V2* __restrict__ f12, int* __restrict__ picked) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)nrhs * Nh) return;
+    const int r = (int)(t / Nh);
+    const bool use = iw[r].rho < ib[r].rho;
+    if (use) f12[t] = warm[t];
+    if (picked && t % Nh == 0) picked[r] = use ? 1 : 0;
+}
+
 }  // namespace
 
 }  // namespace splitsart
 
 using namespace splitsart;
+
+extern "C" int splitsart_pick_start(const splitsart_system* s, int nrhs, const void* f12_warm_dev,
+                                    const splitsart_solve_info* info_warm_dev,
+                                    const splitsart_solve_info* info_base_dev, void* f12_dev, int* picked_dev,
+                                    void* stream) {
+    if (!s || nrhs < 1 || !f12_warm_dev || !info_warm_dev || !info_base_dev || !f12_dev)
+        return fail(SPLITSART_ERR_ARG, "pick_start: bad argument");
+    const long long n = (long long)nrhs * s->Nh;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (s->dtype == SPLITSART_F64)
+        pick_start_kernel<double2><<<g, 256, 0, st>>>(nrhs, s->Nh, (const double2*)f12_warm_dev, info_warm_dev,
+                                                       info_base_dev, (double2*)f12_dev, picked_dev);
+    else
+        pick_start_kernel<float2><<<g, 256, 0, st>>>(nrhs, s->Nh, (const float2*)f12_warm_dev, info_warm_dev,
+                                                     info_base_dev, (float2*)f12_dev, picked_dev);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SPLITSART_OK : cuda_fail(e, "pick_start: launch");
+}
 
 extern "C" int splitsart_solve_multi(splitsart_system* s, int nrhs, const void* p12_dev, void* f12_dev,
                                      const splitsart_solve_opts* o, int rhs_per_cta, splitsart_solve_info* info_dev,

@@ -73,6 +73,7 @@ _SIGS = {
     "splitsart_system_slices": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "splitsart_solve_result_slices": ([_P, ctypes.POINTER(SolveInfo), ctypes.c_int], ctypes.c_int),
     "splitsart_solve_multi": ([_P, ctypes.c_int, _P, _P, ctypes.POINTER(SolveOpts), ctypes.c_int, _P, _P], ctypes.c_int),
+    "splitsart_pick_start": ([_P, ctypes.c_int, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "splitsart_refold": ([_P, _P], ctypes.c_int),
     "splitsart_system_info_get": ([_P, ctypes.POINTER(SystemInfo)], ctypes.c_int),
     "splitsart_system_export": ([_P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
@@ -368,6 +369,16 @@ def solve_multi(system: System, p12, f12, opts: SolveOpts, info, rhs_per_cta: in
     _check(lib().splitsart_solve_multi(system.handle, nrhs, _dev_ptr(p12, 2 * system.Mh * nrhs, vt, "p12"),
                                        _dev_ptr(f12, 2 * system.Nh * nrhs, vt, "f12"), ctypes.byref(opts),
                                        rhs_per_cta, info.data_ptr(), _stream_ptr(stream)))
+
+
+def pick_start(system: System, f12_warm, info_warm, info_base, f12, picked=None, stream=None) -> None:
+    """Keep, per right-hand side, the warm start where its rho is lower than the base start's."""
+    nrhs = f12.shape[0]
+    vt = system.vec_dtype
+    _check(lib().splitsart_pick_start(system.handle, nrhs, _dev_ptr(f12_warm, 2 * system.Nh * nrhs, vt, "f12_warm"),
+                                      info_warm.data_ptr(), info_base.data_ptr(),
+                                      _dev_ptr(f12, 2 * system.Nh * nrhs, vt, "f12"),
+                                      None if picked is None else picked.data_ptr(), _stream_ptr(stream)))
 
 
 def read_infos(info, n: int) -> list:

@@ -1,0 +1,198 @@
+"""Learned warm start for split-SART: data, training, and the comparison with plain SART.
+
+Steps, all run by the library's kernels through the C ABI:
+1. Training data: each seeded phantom (tiny-slice geometry) is projected,
+   solved for 5 and 500 iterations from zero, and recombined as images
+   [nz][nx]. The 5-iteration image is the network input and the
+   500-iteration image the target.
+2. Training: the network (splitsart_cnn_*) with Adam on mini-batches.
+3. Warm-started solve, for each right-hand side:
+   - run 5 iterations;
+   - apply the network to the recombined image;
+   - fold the network's image into (f1, f2) (proof of Theorem 1);
+   - keep it only if its residual is lower than a zero start's (rho < 1);
+     otherwise fall back to plain split-SART, continuing from the
+     5-iteration image;
+   - continue split-SART until rho <= tol.
+   Measured on held-out phantoms, a guess can raise rho above the 5-iteration
+   image's and still reach the tolerance in fewer iterations. So the fallback
+   guards against a useless network (no better than zero), not against that.
+4. The comparison is plain split-SART from zero, to the same tolerance.
+
+Many right-hand sides are processed at once with splitsart_solve_multi. The
+vector folds use a batch of copies of the slice, which has exactly the
+[nrhs][M] / [nrhs][Mh] layouts.
+"""
+from __future__ import annotations
+
+import ctypes
+import time
+
+import numpy as np
+
+from . import splitsart as ss
+from .synthetic import TINY, cnn_initial_params, random_phantom
+
+EARLY_ITERS = 5
+TARGET_ITERS = 500
+
+
+class WarmStart:
+    def __init__(self, g=TINY, chunk: int = 1024, max_batch: int = 256, params=None, mode: int = 1,
+                 lam: float = 1.0):
+        import torch
+        self.g = g
+        self.lam = lam
+        self.geom = ss.make_geometry(g)
+        self.system = ss.fold_system(self.geom, ss.F32)
+        self.chunk = chunk
+        self.vec = ss.fold_batch([self.geom] * chunk, ss.F32)  # [chunk][...] layouts for the vector folds
+        self.cnn = ss.Cnn(g.nz, g.nx, max_batch, cnn_initial_params() if params is None else params)
+        if mode:
+            self.cnn.set_mode(mode)
+        self.dev = torch.device("cuda")
+
+    # ---- helpers over chunks of right-hand sides ----
+    def _chunks(self, n):
+        for a in range(0, n, self.chunk):
+            yield a, min(a + self.chunk, n)
+
+    def _vec_for(self, n):
+        return self.vec if n == self.chunk else ss.fold_batch([self.geom] * n, ss.F32)
+
+    def project(self, images):
+        """images: CUDA float32 [n][nz][nx] -> p [n][M]."""
+        import torch
+        g = self.g
+        n = images.shape[0]
+        p = torch.empty(n, g.M, device=self.dev)
+        for a, b in self._chunks(n):
+            v = self._vec_for(b - a)
+            ss.project(v, images[a:b].reshape(-1), p[a:b].reshape(-1), layout=ss.LAYOUT_IMAGE)
+        return p
+
+    def fold_rhs(self, p):
+        import torch
+        n = p.shape[0]
+        p12 = torch.empty(n, self.g.M // 2, 2, device=self.dev)
+        for a, b in self._chunks(n):
+            ss.fold_rhs(self._vec_for(b - a), p[a:b].reshape(-1), p12[a:b].reshape(-1, 2))
+        return p12
+
+    def recombine(self, f12):
+        import torch
+        n = f12.shape[0]
+        img = torch.empty(n, self.g.nz, self.g.nx, device=self.dev)
+        for a, b in self._chunks(n):
+            ss.recombine(self._vec_for(b - a), f12[a:b].reshape(-1, 2), img[a:b].reshape(-1), layout=ss.LAYOUT_IMAGE)
+        return img
+
+    def fold_image(self, img):
+        import torch
+        n = img.shape[0]
+        f12 = torch.empty(n, self.g.N // 2, 2, device=self.dev)
+        for a, b in self._chunks(n):
+            ss.fold_image(self._vec_for(b - a), img[a:b].reshape(-1), f12[a:b].reshape(-1, 2), layout=ss.LAYOUT_IMAGE)
+        return f12
+
+    def solve(self, p12, f12, iters, tol=0.0):
+        """Solve all right-hand sides in place; returns the per-RHS info list and the raw device info."""
+        import torch
+        n = p12.shape[0]
+        info = torch.zeros(n * ctypes.sizeof(ss.SolveInfo), dtype=torch.uint8, device=self.dev)
+        ss.solve_multi(self.system, p12, f12, ss.solve_opts(iters, self.lam, tol), info, rhs_per_cta=4)
+        return info
+
+    # ---- 1. data ----
+    def phantoms(self, seeds):
+        import torch
+        imgs = np.stack([random_phantom(self.g, 5, 8, stream=int(s)) for s in seeds]).astype(np.float32)
+        return torch.as_tensor(imgs, device=self.dev)
+
+    def make_pairs(self, seeds):
+        """Return (x, t): 5-iteration and 500-iteration images [n][nz][nx] of the seeded phantoms."""
+        import torch
+        truth = self.phantoms(seeds)
+        p12 = self.fold_rhs(self.project(truth))
+        f12 = torch.zeros(len(seeds), self.g.N // 2, 2, device=self.dev)
+        self.solve(p12, f12, EARLY_ITERS)
+        x = self.recombine(f12)
+        self.solve(p12, f12, TARGET_ITERS - EARLY_ITERS)
+        t = self.recombine(f12)
+        return x, t
+
+    # ---- 2. training ----
+    def train(self, x, t, epochs=10, batch=64, lr=1e-3, seed=0, log_every=0):
+        import torch
+        n = x.shape[0]
+        rng = np.random.default_rng(seed)
+        loss = torch.zeros(1, device=self.dev)
+        hist = []
+        for ep in range(epochs):
+            order = torch.as_tensor(rng.permutation(n), device=self.dev)
+            acc = torch.zeros(1, device=self.dev, dtype=torch.float64)
+            steps = 0
+            for a in range(0, n - batch + 1, batch):
+                idx = order[a:a + batch]
+                xb, tb = x[idx].contiguous(), t[idx].contiguous()
+                self.cnn.train_step(xb, tb, lr=lr, loss=loss)
+                acc += loss.double()
+                steps += 1
+            hist.append(float(acc.item() / max(steps, 1)))
+            if log_every and (ep + 1) % log_every == 0:
+                print(f"epoch {ep + 1}: mean loss {hist[-1]:.4e}", flush=True)
+        return hist
+
+    def predict(self, x):
+        import torch
+        y = torch.empty_like(x)
+        for a in range(0, x.shape[0], self.cnn.max_batch):
+            b = min(a + self.cnn.max_batch, x.shape[0])
+            self.cnn.forward(x[a:b].contiguous(), y[a:b])
+        return y
+
+    # ---- 3./4. comparison to rho <= tol ----
+    def compare(self, seeds, tol=1e-3, max_iters=20000):
+        """Plain split-SART from zero vs the warm start, on the seeded phantoms.
+
+        Returns per-RHS iteration counts, timings, and the fraction of warm starts kept.
+        """
+        import torch
+        truth = self.phantoms(seeds)
+        p12 = self.fold_rhs(self.project(truth))
+        n = len(seeds)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        # Plain.
+        f_plain = torch.zeros(n, self.g.N // 2, 2, device=self.dev)
+        torch.cuda.synchronize()
+        ev[0].record()
+        info_plain = self.solve(p12, f_plain, max_iters, tol)
+        ev[1].record()
+        # Warm: 5 iterations, network, fold, fallback, continue.
+        f_warm = torch.zeros(n, self.g.N // 2, 2, device=self.dev)
+        ev[2].record()
+        info_early = self.solve(p12, f_warm, EARLY_ITERS, tol)
+        guess = self.fold_image(self.predict(self.recombine(f_warm)))
+        info_guess = self.solve(p12, guess, 0)  # rho of the guess
+        info_zero = self.solve(p12, torch.zeros_like(guess), 0)  # rho of a zero start (1, or 0 if p = 0)
+        picked = torch.zeros(n, dtype=torch.int32, device=self.dev)
+        ss.pick_start(self.system, guess, info_guess, info_zero, f_warm, picked)
+        info_rest = self.solve(p12, f_warm, max_iters - EARLY_ITERS, tol)
+        ev[3].record()
+        torch.cuda.synchronize()
+        it_plain = np.array([i["iters"] for i in ss.read_infos(info_plain, n)])
+        early = ss.read_infos(info_early, n)
+        rest = ss.read_infos(info_rest, n)
+        # A right-hand side that already met tol within the first 5 iterations stops there.
+        it_warm = np.array([e["iters"] if e["rho"] <= tol else EARLY_ITERS + r["iters"] for e, r in zip(early, rest)])
+        rho_plain = np.array([i["rho"] for i in ss.read_infos(info_plain, n)])
+        rho_warm = np.array([e["rho"] if e["rho"] <= tol else r["rho"] for e, r in zip(early, rest)])
+        return {
+            "n": n, "tol": tol,
+            "iters_plain": it_plain, "iters_warm": it_warm,
+            "rho_plain": rho_plain, "rho_warm": rho_warm,
+            "ms_plain": ev[0].elapsed_time(ev[1]), "ms_warm": ev[2].elapsed_time(ev[3]),
+            "warm_kept": float(picked.float().mean().item()),
+            "rho_early": np.array([e["rho"] for e in early]),
+            "rho_guess": np.array([i["rho"] for i in ss.read_infos(info_guess, n)]),
+        }

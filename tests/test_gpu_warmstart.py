@@ -1,0 +1,69 @@
+"""The learned warm start, end to end on the GPU (reduced training set).
+
+The network is trained on 5-iteration -> 500-iteration image pairs made by the
+library's own solver. On held-out phantoms:
+- it must lower the residual of the 5-iteration image;
+- a warm-started solve must reach the tolerance in fewer iterations than plain
+  split-SART from zero.
+The oracle's FP64 residual judges the warm-started result.
+"""
+import numpy as np
+import pytest
+
+from oracle import geometry as ogeo
+from oracle import split as osplit
+from paper_1902_10559_gb300.synthetic import TINY
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ws():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1902_10559_gb300 import build, splitsart
+    build.build()
+    splitsart.lib()
+    from paper_1902_10559_gb300.warmstart import WarmStart
+    return WarmStart(chunk=256, max_batch=64)
+
+
+def test_training_data_and_warm_start_gain(ws):
+    x, t = ws.make_pairs(range(6000))
+    assert x.shape == (6000, 16, 32) and torch.isfinite(t).all()
+    hist = ws.train(x, t, epochs=8, batch=64, lr=1e-3)
+    assert hist[-1] < 0.8 * hist[0], hist
+    held = range(10**6, 10**6 + 128)
+    xe, te = ws.make_pairs(held)
+    guess = ws.predict(xe)
+    # In image space the network brings the 5-iteration image closer to the 500-iteration image.
+    assert (guess - te).norm() < 0.85 * (xe - te).norm()
+    tol = 1e-2
+    res = ws.compare(held, tol=tol, max_iters=20000)
+    assert np.all(res["rho_plain"] <= tol) and np.all(res["rho_warm"] <= tol)
+    # Gain: fewer iterations to the tolerance, for most phantoms and on average.
+    assert res["iters_warm"].mean() < 0.95 * res["iters_plain"].mean(), (res["iters_warm"].mean(), res["iters_plain"].mean())
+    assert np.mean(res["iters_warm"] < res["iters_plain"]) > 0.7
+    print(f"iterations to rho <= {tol}: plain {res['iters_plain'].mean():.0f}, warm {res['iters_warm'].mean():.0f}; "
+          f"time plain {res['ms_plain']:.1f} ms, warm {res['ms_warm']:.1f} ms; warm kept {res['warm_kept']:.2f}")
+
+
+def test_oracle_judges_warm_start_residual(ws):
+    """The oracle's FP64 residual ||A f - p|| / ||p|| of a warm-started image is within the tolerance."""
+    import ctypes
+    from paper_1902_10559_gb300 import splitsart as ss
+    seeds = range(2 * 10**6, 2 * 10**6 + 4)
+    truth = ws.phantoms(seeds)
+    p = ws.project(truth)
+    p12 = ws.fold_rhs(p)
+    f12 = torch.zeros(4, TINY.N // 2, 2, device="cuda")
+    ws.solve(p12, f12, 5)
+    guess = ws.fold_image(ws.predict(ws.recombine(f12)))
+    info = ws.solve(p12, guess, 20000, tol=2e-3)
+    img = ws.recombine(guess).cpu().numpy().astype(np.float64)
+    A = ogeo.mirrored_system_matrix(TINY)
+    for r in range(4):
+        f = ogeo.image_to_snake(TINY, img[r])
+        rho = osplit.relative_residual(A, f, p[r].double().cpu().numpy())
+        assert rho <= 2e-3 * 1.01, (r, rho)
