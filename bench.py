@@ -184,6 +184,19 @@ class Realistic:
     name = "realistic"
     config_id = 2
     profile = "sart_resident_realistic_fp32.txt"
+    iters = ITERS
+    lam = LAMBDA
+    metric, unit, higher_is_better, dtype = METRIC, UNIT, True, "f32"
+
+    def extra(self, ss):
+        """Workload-specific keys added to the JSON line."""
+        return {}
+
+    def oracle_run(self, osart, case):
+        """One oracle solve of a sampled case; returns the units it completed."""
+        n, A1, A2, p1, p2 = case
+        osart.split_sart(A1, A2, p1, p2, self.lam, self.iters)
+        return n * self.iters
 
     def setup(self, ss, dev, rank):
         import torch
@@ -200,7 +213,7 @@ class Realistic:
         self.f = torch.empty(g.N, device=dev)
         ss.fold_rhs(self.system, self.p, self.p12)
         self.tuned = autotune.tune_solve(self.system, self.p12, self.f12)
-        self.opts = ss.solve_opts(ITERS, LAMBDA, **self.tuned)
+        self.opts = ss.solve_opts(self.iters, self.lam, **self.tuned)
         self.launches = FOLD_LAUNCHES + 3
 
     def step(self, ss, p_in, f_out, layout, ev=None):
@@ -219,7 +232,7 @@ class Realistic:
 
     def roofline(self, ss, solve_ms):
         S, Mh, Nh = self.info["S"], self.system.Mh, self.system.Nh
-        alg = algorithmic_bytes_per_launch(S, Mh, Nh, ITERS)
+        alg = algorithmic_bytes_per_launch(S, Mh, Nh, self.iters)
         peak, kind = read_peak("hbm_gbs", 6800.0)
         ach = alg / (solve_ms / 1e3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
@@ -232,8 +245,8 @@ class Realistic:
     def config(self):
         return {"workload": "realistic slice: 512x128 voxels, K=26 sources +/-25 deg, 1024 bins, 20 ellipses, "
                             "1% noise, 200 iterations, lambda=0.8, fp32",
-                "nx": self.g.nx, "nz": self.g.nz, "N": self.g.N, "M": self.g.M, "iterations": ITERS,
-                "lambda": LAMBDA, "S": self.info["S"], "launch": self.tuned,
+                "nx": self.g.nx, "nz": self.g.nz, "N": self.g.N, "M": self.g.M, "iterations": self.iters,
+                "lambda": self.lam, "S": self.info["S"], "launch": self.tuned,
                 "l2": "flushed between timed steps (256 MiB write)"}
 
     def oracle_case(self, budget_s):
@@ -271,7 +284,7 @@ class Batch(Realistic):
         self.f = torch.empty(sysm.N, device=dev)
         ss.fold_rhs(sysm, self.p, self.p12)
         self.tuned = autotune.tune_solve(sysm, self.p12, self.f12, iters=3)
-        self.opts = ss.solve_opts(ITERS, LAMBDA, **self.tuned)
+        self.opts = ss.solve_opts(self.iters, self.lam, **self.tuned)
         self.launches = FOLD_LAUNCHES + 3
         # The reconstruction after the fold of A, captured once as a CUDA graph and replayed per step.
         self.p_in = self.p
@@ -308,7 +321,7 @@ class Batch(Realistic):
 
     def roofline(self, ss, solve_ms):
         S, Mh, Nh = self.info["S"], self.system.Mh, self.system.Nh
-        alg = algorithmic_bytes_per_launch(S, Mh, Nh, ITERS, batch_rows=Mh)
+        alg = algorithmic_bytes_per_launch(S, Mh, Nh, self.iters, batch_rows=Mh)
         # The timed graph also holds fold_rhs and recombine (about 0.1% of its bytes).
         peak, kind = read_peak("hbm_gbs", 6800.0)
         ach = alg / (solve_ms / 1e3) / 1e9
@@ -321,7 +334,7 @@ class Batch(Realistic):
         return {"workload": f"batch: {len(self.gs)} slices, nx in {{256,512,768,1024}}, nz in [64,256], K in [16,32], "
                             "nb=2nx, 200 iterations, lambda=0.8, fp32, one persistent launch in a CUDA graph",
                 "slices": len(self.gs), "N": self.system.N, "M": self.system.M, "S": self.info["S"],
-                "iterations": ITERS, "lambda": LAMBDA, "launch": self.tuned,
+                "iterations": self.iters, "lambda": self.lam, "launch": self.tuned,
                 "l2": "inputs larger than L2 (about 10 GB per iteration), L2 also flushed between steps"}
 
     def oracle_case(self, budget_s):
@@ -346,6 +359,7 @@ class Multi(Realistic):
     config_id = 3
     profile = "sart_multi_tiny64_fp32.txt"
     NRHS = 64
+    ktype = "TF32"
 
     def setup(self, ss, dev, rank):
         import torch
@@ -365,7 +379,7 @@ class Multi(Realistic):
         self.infobuf = torch.zeros(self.NRHS * ctypes.sizeof(ss.SolveInfo), dtype=torch.uint8, device=dev)
         ss.fold_rhs(self.vec, self.p, self.p12.view(-1, 2))
         self.tuned = autotune.tune_multi(self.system, self.p12, self.f12)
-        self.opts = ss.solve_opts(ITERS, LAMBDA, block_threads=self.tuned["block_threads"])
+        self.opts = ss.solve_opts(self.iters, self.lam, block_threads=self.tuned["block_threads"])
         self.launches = FOLD_LAUNCHES + 3
 
     def step(self, ss, p_in, f_out, layout, ev=None):
@@ -385,19 +399,19 @@ class Multi(Realistic):
 
     def roofline(self, ss, solve_ms):
         S = self.info["S"]
-        flops = 8.0 * S * self.NRHS * ITERS  # 2 systems x FMA x (forward + back)
+        flops = 8.0 * S * self.NRHS * self.iters  # 2 systems x FMA x (forward + back)
         # FP32 CUDA-core FMA peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         ach = flops / (solve_ms / 1e3) / 1e12
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": profile_traffic(self.profile), "kernel": "sart_multi_kernel<TF32,RC>",
+                "traffic": profile_traffic(self.profile), "kernel": f"sart_multi_kernel<{self.ktype},RC>",
                 "peak_source": "nominal FP32 FMA rate at 2.07 GHz",
                 "note": "system and vectors in shared memory; latency- and shared-memory-bound, not DRAM"}
 
     def config(self):
         return {"workload": "64 right-hand sides on the tiny slice geometry (32x16 voxels, M=640), 200 iterations, "
                             "lambda=0.8, fp32, SpMM", "nrhs": self.NRHS, "N": self.g.N, "M": self.g.M,
-                "S": self.info["S"], "iterations": ITERS, "launch": self.tuned,
+                "S": self.info["S"], "iterations": self.iters, "launch": self.tuned,
                 "l2": "flushed between timed steps (256 MiB write)"}
 
     def oracle_case(self, budget_s):
@@ -414,7 +428,216 @@ class Multi(Realistic):
         return cases, "all 64 right-hand sides"
 
 
-WORKLOADS = {"realistic": Realistic, "batch": Batch, "multi": Multi}
+class Precision(Multi):
+    """Matrix values stored as BF16 (timed) and FP16, with per-row FP32 scales.
+
+    The step is the 64-right-hand-side tiny-slice SpMM for 500 iterations,
+    lambda = 1, with BF16 values. The line adds, for FP32, BF16 and FP16
+    storage, the iterations and time to rho <= 1e-3, and each reduced form's
+    distance from the FP32 result after 500 iterations. Errors against the
+    FP64 oracle are checked in the precision tests.
+    """
+    name = "precision"
+    config_id = 4
+    profile = "sart_multi_tiny64_bf16.txt"
+    iters = 500
+    lam = 1.0
+    ktype = "TBF16"
+    dtype = "bf16 values, f32 accumulation"
+    TOL = 1e-3
+    MAX_ITERS = 30000
+
+    def setup(self, ss, dev, rank):
+        from paper_1902_10559_gb300 import autotune
+        super().setup(ss, dev, rank)
+        self.forms = {"f32": (self.system, self.tuned),
+                      "bf16": (ss.fold_system(self.geom, ss.BF16), None),
+                      "f16": (ss.fold_system(self.geom, ss.F16), None)}
+        for k in ("bf16", "f16"):
+            sysm = self.forms[k][0]
+            self.forms[k] = (sysm, autotune.tune_multi(sysm, self.p12, self.f12))
+        self.system, self.tuned = self.forms["bf16"]
+        self.info = self.system.info()
+        self.opts = ss.solve_opts(self.iters, self.lam, block_threads=self.tuned["block_threads"])
+
+    def extra(self, ss):
+        import numpy as np
+        import torch
+        out = {}
+        finals = {}
+        for name, (sysm, tuned) in self.forms.items():
+            # 500 iterations, for the distance between forms.
+            f12 = torch.zeros_like(self.f12)
+            ss.solve_multi(sysm, self.p12, f12, ss.solve_opts(self.iters, self.lam,
+                                                              block_threads=tuned["block_threads"]),
+                           self.infobuf, rhs_per_cta=tuned["rhs_per_cta"])
+            img = torch.empty(self.NRHS * self.g.N, device=f12.device)
+            ss.recombine(self.vec, f12.view(-1, 2), img, layout=ss.LAYOUT_IMAGE)
+            finals[name] = img.double()
+            # To rho <= 1e-3.
+            opts = ss.solve_opts(self.MAX_ITERS, self.lam, self.TOL, block_threads=tuned["block_threads"])
+            ts = []
+            for _ in range(3):
+                f12.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                ss.solve_multi(sysm, self.p12, f12, opts, self.infobuf, rhs_per_cta=tuned["rhs_per_cta"])
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            infos = ss.read_infos(self.infobuf, self.NRHS)
+            its = np.array([i["iters"] for i in infos])
+            reached = np.array([i["rho"] <= self.TOL for i in infos])
+            out[name] = {"ms": float(np.median(ts)), "iters_mean": float(its.mean()), "iters_max": int(its.max()),
+                         "reached": float(reached.mean()), "launch": tuned}
+        for name in ("bf16", "f16"):
+            d = torch.linalg.vector_norm(finals[name] - finals["f32"]) / torch.linalg.vector_norm(finals["f32"])
+            out[name]["rel_diff_vs_f32_at_500"] = float(d)
+        for name in ("bf16", "f16"):
+            out[name]["time_vs_f32"] = out[name]["ms"] / out["f32"]["ms"]
+        return {"time_to_rho_1e-3": out,
+                "note": "64 right-hand sides, one solve_multi launch each; ms is the launch time until the last "
+                        "right-hand side stops; errors against the FP64 oracle are in the precision tests"}
+
+    def config(self):
+        c = super().config()
+        c["workload"] = ("64 right-hand sides on the tiny slice geometry (32x16 voxels, M=640), 500 iterations, "
+                         "lambda=1, BF16 matrix values with per-row FP32 scales, FP32 accumulation, SpMM")
+        return c
+
+
+class Warmstart(Multi):
+    """Learned warm start against plain split-SART, both to rho <= 1e-3.
+
+    Setup: 20000 seeded training phantoms on the tiny slice geometry; inputs
+    are the 5-iteration images and targets the 500-iteration images, all made
+    by the library's solver; the network is trained with the library's
+    kernels (Adam, batch 64). The step reconstructs 512 held-out phantoms
+    (seeds 10^6 + k) to rho <= 1e-3: 5 iterations, network, fold of the
+    image, fallback test, then split-SART to the tolerance, and the Theorem 1
+    recombination. The line adds the plain solve of the same 512 from zero.
+    """
+    name = "warmstart"
+    config_id = 5
+    profile = "sart_multi_tiny64_fp32.txt"
+    iters = 30000  # iteration cap
+    lam = 1.0
+    metric = "split-SART reconstructions to relative residual 1e-3 per second"
+    unit = "reconstructions/s"
+    dtype = "f32 solve, bf16 tensor-core convolutions"
+    TOL = 1e-3
+    N_TRAIN = 20000
+    N_HELD = 512
+    EPOCHS = 6
+
+    def setup(self, ss, dev, rank):
+        import numpy as np
+        import torch
+        from paper_1902_10559_gb300.synthetic import TINY
+        from paper_1902_10559_gb300.warmstart import WarmStart
+        self.g = TINY
+        self.ws = WarmStart(TINY, lam=self.lam)
+        self.system = self.ws.system
+        self.info = self.system.info()
+        t0 = time.perf_counter()
+        x, t = self.ws.make_pairs(np.arange(self.N_TRAIN))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        self.loss_hist = self.ws.train(x, t, epochs=self.EPOCHS, batch=64, lr=1e-3)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        self.setup_s = {"training_pairs": t1 - t0, "training": t2 - t1}
+        del x, t
+        held = np.arange(10 ** 6, 10 ** 6 + self.N_HELD)
+        self.p = self.ws.project(self.ws.phantoms(held)).reshape(-1).contiguous()
+        self.f = torch.empty(self.N_HELD * TINY.N, device=dev)
+        self.launches = 0  # counted per step below
+        self._infos = None
+
+    def step(self, ss, p_in, f_out, layout, ev=None):
+        ss.refold(self.system)
+        p12 = self.ws.fold_rhs(p_in.view(self.N_HELD, -1))
+        if ev:
+            ev[0].record()
+        f12, e, r, picked = self.ws.solve_warm(p12, self.TOL, self.iters)
+        if ev:
+            ev[1].record()
+        self._infos = (e, r)
+        f_out.view(self.N_HELD, -1).copy_(self.ws.recombine(f12).view(self.N_HELD, -1))
+
+    def units(self, ss):
+        return self.N_HELD
+
+    def _counts(self, ss):
+        e, r = self._infos
+        return self.ws.warm_counts(ss.read_infos(e, self.N_HELD), ss.read_infos(r, self.N_HELD), self.TOL)
+
+    def roofline(self, ss, solve_ms):
+        its, _ = self._counts(ss)
+        flops = 8.0 * self.info["S"] * float(its.sum())
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        ach = flops / (solve_ms / 1e3) / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": "sart_multi_kernel<TF32,RC> (the solves dominate the warm pipeline)",
+                "peak_source": "nominal FP32 FMA rate at 2.07 GHz",
+                "note": "useful FMAs of the iterations each right-hand side needed, over the whole warm pipeline"}
+
+    def extra(self, ss):
+        import numpy as np
+        import torch
+        its_w, rho_w = self._counts(ss)
+        p12 = self.ws.fold_rhs(self.p.view(self.N_HELD, -1))
+        ts = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            _, info = self.ws.solve_plain(p12, self.TOL, self.iters)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        plain = ss.read_infos(info, self.N_HELD)
+        its_p = np.array([i["iters"] for i in plain])
+        # Launches of one warm step: fold of A (21), fold of p, 5 iterations, recombine, CNN (4 per 256 images),
+        # fold of the image, two rho-only solves, pick, continuation, recombine.
+        self.launches = FOLD_LAUNCHES + 1 + 1 + 1 + 4 * ((self.N_HELD + 255) // 256) + 1 + 2 + 1 + 1 + 1
+        return {
+            "plain": {"ms": float(np.median(ts)), "iters_mean": float(its_p.mean()),
+                      "iters_median": float(np.median(its_p)), "reached": float(np.mean([i["rho"] <= self.TOL
+                                                                                       for i in plain]))},
+            "warm": {"iters_mean": float(its_w.mean()), "iters_median": float(np.median(its_w)),
+                     "reached": float(np.mean(rho_w <= self.TOL)),
+                     "fewer_iters_frac": float(np.mean(its_w < its_p))},
+            "training": {"pairs": self.N_TRAIN, "epochs": self.EPOCHS, "batch": 64, "lr": 1e-3,
+                         "loss_first_epoch": self.loss_hist[0], "loss_last_epoch": self.loss_hist[-1],
+                         "seconds": self.setup_s},
+        }
+
+    def config(self):
+        return {"workload": "learned warm start: 512 held-out phantoms on the tiny slice geometry (32x16 voxels, "
+                            "M=640) reconstructed to rho <= 1e-3, lambda=1, network trained on 20000 phantoms",
+                "nrhs": self.N_HELD, "N": self.g.N, "M": self.g.M, "S": self.info["S"], "tol": self.TOL,
+                "max_iters": self.iters, "l2": "flushed between timed steps (256 MiB write)"}
+
+    def oracle_case(self, budget_s):
+        from oracle import geometry as ogeo
+        from oracle import split as osplit
+        from paper_1902_10559_gb300.synthetic import TINY, random_phantom
+        A = ogeo.mirrored_system_matrix(TINY)
+        A1, A2 = osplit.fold_matrix(A)
+        cases = []
+        for r in range(8):
+            f_true = ogeo.image_to_snake(TINY, random_phantom(TINY, 5, 8, stream=10 ** 6 + r))
+            p1, p2 = osplit.fold_rhs(A @ f_true)
+            cases.append((1, A1, A2, p1, p2))
+        return cases, "held-out phantoms"
+
+    def oracle_run(self, osart, case):
+        _, A1, A2, p1, p2 = case
+        osart.split_sart(A1, A2, p1, p2, self.lam, self.iters, self.TOL)
+        return 1
+
+
+WORKLOADS = {"realistic": Realistic, "batch": Batch, "multi": Multi, "precision": Precision, "warmstart": Warmstart}
 
 
 # ---------------------------------------------------------------------------
@@ -429,18 +652,17 @@ def oracle_throughput(wl, budget_s):
     done = 0
     units = 0
     while True:
-        for n, A1, A2, p1, p2 in cases:
-            osart.split_sart(A1, A2, p1, p2, LAMBDA, ITERS)
-            units += n * ITERS
+        for case in cases:
+            units += wl.oracle_run(osart, case)
             done += 1
             if time.perf_counter() - t0 >= budget_s:
                 break
         if time.perf_counter() - t0 >= budget_s:
             break
     el = time.perf_counter() - t0
-    return units / el, {"value": units / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-                        "sample": f"{done} full {ITERS}-iteration FP64 solves from {what} (SciPy CSR, single "
-                                  f"thread), {el:.1f} s; host has {os.cpu_count()} cores"}
+    return units / el, {"value": units / el, "unit": wl.unit, "cores": 1, "kind": "oracle",
+                        "sample": f"{done} full FP64 solves ({wl.iters}-iteration cap) from {what} (SciPy CSR, "
+                                  f"single thread), {el:.1f} s; host has {os.cpu_count()} cores"}
 
 
 def run_native(args):
@@ -522,18 +744,21 @@ def run_native(args):
     total_units = units * args.steps * ws
     value = total_units / (step_ms / 1e3)
     e2e_value = total_units / (e2e_ms / 1e3)
+    extra = wl.extra(ss)
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": step_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic (seeded random ellipses, Siddon projections)",
+        "metric": wl.metric, "value": value, "unit": wl.unit, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": wl.higher_is_better,
+        "scaling": "weak", "vs_baseline": None, "dtype": wl.dtype,
+        "data": "synthetic (seeded random ellipses, Siddon projections)",
         "config": wl.config(),
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": wl.p.numel() * 4,
+        "e2e": {"value": e2e_value, "unit": wl.unit, "h2d_bytes_per_step": wl.p.numel() * 4,
                 "d2h_bytes_per_step": wl.f.numel() * 4},
         "gpu_launches": wl.launches * args.steps,
         "roofline": wl.roofline(ss, solve_ms),
         "clocks": clocks.summary(),
         "breakdown_ms": {"solve": solve_ms, "fold_A": fold_ms, "step": step_ms / args.steps},
     }
+    out.update(extra)
     if rank == 0 and not args.no_cpu_baseline:
         _, out["cpu_baseline"] = oracle_throughput(wl, args.cpu_seconds)
     if rank == 0:
@@ -551,23 +776,24 @@ def run_reference(args):
     cases, what = wl.oracle_case(0)
     for _ in range(args.warmup):
         n, A1, A2, p1, p2 = cases[0]
-        osart.split_sart(A1, A2, p1, p2, LAMBDA, 5)  # short warm-up solves
+        osart.split_sart(A1, A2, p1, p2, wl.lam, 5)  # short warm-up solves
     t0 = time.perf_counter()
     units = 0
     for _ in range(args.steps):
-        for n, A1, A2, p1, p2 in cases:
-            osart.split_sart(A1, A2, p1, p2, LAMBDA, ITERS)
-            units += n * ITERS
+        for case in cases:
+            units += wl.oracle_run(osart, case)
     total = time.perf_counter() - t0
     value = units / total
-    cfg = {"workload": f"oracle on {what} of the {args.workload} workload", "iterations": ITERS, "lambda": LAMBDA}
-    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"{args.steps} x {what}, full {ITERS}-iteration solves (SciPy CSR, single "
-                                      f"thread); host has {os.cpu_count()} cores"},
-           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    cfg = {"workload": f"oracle on {what} of the {args.workload} workload", "iterations": wl.iters,
+           "lambda": wl.lam}
+    out = {"impl": "reference", "metric": wl.metric, "value": value, "unit": wl.unit, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+           "higher_is_better": wl.higher_is_better, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": cfg,
+           "cpu_baseline": {"value": value, "unit": wl.unit, "cores": 1, "kind": "oracle",
+                            "sample": f"{args.steps} x {what}, full solves ({wl.iters}-iteration cap; SciPy CSR, "
+                                      f"single thread); host has {os.cpu_count()} cores"},
+           "e2e": {"value": value, "unit": wl.unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 

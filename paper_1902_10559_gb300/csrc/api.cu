@@ -226,6 +226,8 @@ int create_system(const splitsart_geometry* const* geoms, int ns, int dtype, cud
         {(void**)&s->invR, nb * Mh},
         {(void**)&s->invC, nb * Nh},
         {(void**)&s->scale, quant ? sizeof(float2) * Mh : 0},
+        {(void**)&s->wR, quant ? sizeof(float2) * Mh : 0},
+        {(void**)&s->wC, quant ? sizeof(float2) * Nh : 0},
         {(void**)&s->nzr, sizeof(int32_t) * (Mh + 1)},
         {(void**)&s->nzrp, sizeof(int32_t) * (Mh + 1)},
         {(void**)&s->zr, sizeof(int32_t) * (Mh + 1)},

@@ -17,12 +17,20 @@ namespace splitsart {
 // Value traits. The two split systems always travel together: matrix values
 // and vectors are stored as interleaved pairs (x1, x2). One pass over the
 // shared index pattern then serves A1 and A2 at once.
+//
+// Norm2 is the stored type of the normalisers 1/R and 1/C. KNorm2 is the
+// type the iteration applies. For BF16/FP16 the FP64 normalisers are kept
+// for export, and the kernels read FP32 copies: 1/R times the row scale,
+// and 1/C, each an FP64 value rounded once to FP32. Then u and f cost no
+// FP64 arithmetic (FP64 runs at a small fraction of the FP32 rate on this
+// GPU).
 // ---------------------------------------------------------------------------
 struct TF64 {
     using Pair = double2;  // (a1, a2)
     using Acc = double;
     using Vec2 = double2;  // (x1, x2) vectors: f, p, u
     using Norm2 = double2; // 1/R, 1/C
+    using KNorm2 = double2;
     static constexpr bool kQuant = false;
     static constexpr int kDtype = SPLITSART_F64;
     __device__ static inline void decode(Pair v, Acc& a1, Acc& a2) { a1 = v.x; a2 = v.y; }
@@ -32,6 +40,7 @@ struct TF32 {
     using Acc = float;
     using Vec2 = float2;
     using Norm2 = float2;
+    using KNorm2 = float2;
     static constexpr bool kQuant = false;
     static constexpr int kDtype = SPLITSART_F32;
     __device__ static inline void decode(Pair v, Acc& a1, Acc& a2) { a1 = v.x; a2 = v.y; }
@@ -41,6 +50,7 @@ struct TBF16 {
     using Acc = float;
     using Vec2 = float2;
     using Norm2 = double2;
+    using KNorm2 = float2;
     static constexpr bool kQuant = true;
     static constexpr int kDtype = SPLITSART_BF16;
     __device__ static inline void decode(Pair v, Acc& a1, Acc& a2) {
@@ -57,6 +67,7 @@ struct TF16 {
     using Acc = float;
     using Vec2 = float2;
     using Norm2 = double2;
+    using KNorm2 = float2;
     static constexpr bool kQuant = true;
     static constexpr int kDtype = SPLITSART_F16;
     __device__ static inline void decode(Pair v, Acc& a1, Acc& a2) {
@@ -98,6 +109,25 @@ __device__ __forceinline__ float2 ldcg(const float2* p) { return __ldcg(p); }
 __device__ __forceinline__ double2 ldcg(const double2* p) { return __ldcg(p); }
 __device__ __forceinline__ void stcg(float2* p, float2 v) { __stcg(p, v); }
 __device__ __forceinline__ void stcg(double2* p, double2 v) { __stcg(p, v); }
+
+// One thread's share of ||r||^2. Squares are formed in the working precision
+// and summed in groups of 16 before they join an FP64 total, so FP32 systems
+// take one FP64 add per 16 rows. For FP64 systems every step is FP64.
+template <class Acc>
+struct SqAcc {
+    double tot = 0.0;
+    Acc part = 0;
+    int n = 0;
+    __device__ __forceinline__ void add(Acc x, Acc y) {
+        part += x * x + y * y;
+        if (++n == 16) {
+            tot += (double)part;
+            part = 0;
+            n = 0;
+        }
+    }
+    __device__ __forceinline__ double sum() const { return tot + (double)part; }
+};
 
 template <class T>
 __device__ __forceinline__ T warp_sum(T v, unsigned width = 32) {
@@ -170,6 +200,15 @@ __device__ __forceinline__ bool grid_sync(LaunchCtl* ctl, unsigned target, unsig
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// One warp: the sum of partials[2b + which] over b < nparts, in a fixed
+// order. Every CTA obtains bitwise the same total.
+__device__ __forceinline__ double grid_total(const double* partials, int nparts, int lane, int which) {
+    double t = 0.0;
+#pragma unroll 4
+    for (int b = lane; b < nparts; b += 32) t += __ldcg(partials + 2 * b + which);
+    return warp_sum(t);
 }
 
 // Warp 0: sum the per-CTA pairs partials[2b], partials[2b+1] (b < nparts) in

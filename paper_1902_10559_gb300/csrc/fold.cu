@@ -204,7 +204,7 @@ __global__ void fold_fill_kernel(int64_t Mh, SliceMap sm, const int64_t* __restr
                                  const int32_t* __restrict__ frp, int32_t* __restrict__ col,
                                  typename T::Pair* __restrict__ val, double2* __restrict__ Rsum,
                                  typename T::Norm2* __restrict__ invR, float2* __restrict__ scale,
-                                 FoldStats* __restrict__ stats) {
+                                 float2* __restrict__ wR, FoldStats* __restrict__ stats) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= Mh) return;
     const int sl = slice_of(sm.rows, sm.ns, i);
@@ -238,7 +238,10 @@ __global__ void fold_fill_kernel(int64_t Mh, SliceMap sm, const int64_t* __restr
     Rsum[i] = make_double2(R1, R2);
     using N2 = typename T::Norm2;
     using NS = decltype(N2{}.x);
-    invR[i] = N2{(NS)(R1 > 0.0 ? 1.0 / R1 : 0.0), (NS)(R2 > 0.0 ? 1.0 / R2 : 0.0)};
+    const double i1 = R1 > 0.0 ? 1.0 / R1 : 0.0, i2 = R2 > 0.0 ? 1.0 / R2 : 0.0;
+    invR[i] = N2{(NS)i1, (NS)i2};
+    // What the iteration applies: the row scale times 1/R, rounded once to FP32.
+    if constexpr (T::kQuant) wR[i] = make_float2((float)(i1 * (double)s1), (float)(i2 * (double)s2));
     if (out == frp[i]) atomicAdd(reinterpret_cast<unsigned long long*>(&stats->empty_rows), 1ULL);
     else atomicMax(&stats->max_row, out - frp[i]);
     if (zeros) atomicAdd(reinterpret_cast<unsigned long long*>(&stats->exact_zeros), (unsigned long long)zeros);
@@ -273,7 +276,7 @@ template <class T>
 __global__ void csc_sort_colsum_kernel(int64_t Nh, const int32_t* __restrict__ cp, int32_t* __restrict__ row,
                                        typename T::Pair* __restrict__ valT, const float2* __restrict__ scale,
                                        double2* __restrict__ Csum, typename T::Norm2* __restrict__ invC,
-                                       FoldStats* __restrict__ stats) {
+                                       float2* __restrict__ wC, FoldStats* __restrict__ stats) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= Nh) return;
     const int32_t b = cp[j], e = cp[j + 1];
@@ -306,7 +309,9 @@ __global__ void csc_sort_colsum_kernel(int64_t Nh, const int32_t* __restrict__ c
     if (e > b) atomicMax(&stats->max_col, e - b);
     using N2 = typename T::Norm2;
     using NS = decltype(N2{}.x);
-    invC[j] = N2{(NS)(C1 > 0.0 ? 1.0 / C1 : 0.0), (NS)(C2 > 0.0 ? 1.0 / C2 : 0.0)};
+    const double i1 = C1 > 0.0 ? 1.0 / C1 : 0.0, i2 = C2 > 0.0 ? 1.0 / C2 : 0.0;
+    invC[j] = N2{(NS)i1, (NS)i2};
+    if constexpr (T::kQuant) wC[j] = make_float2((float)i1, (float)i2);
 }
 
 __global__ void nonempty_flags_kernel(int64_t n, const int32_t* __restrict__ ptr, int32_t* __restrict__ flags) {
@@ -360,7 +365,7 @@ int fold_typed(splitsart_system* s, cudaStream_t st) {
     if (rc) return rc;
     if (Mh > 0)
         fold_fill_kernel<T><<<(unsigned)((Mh + 127) / 128), 128, 0, st>>>(
-            Mh, sm, s->hrp, s->hcol, s->hval, s->rp, s->col, (Pair*)s->val, s->Rsum, (N2*)s->invR, s->scale,
+            Mh, sm, s->hrp, s->hcol, s->hval, s->rp, s->col, (Pair*)s->val, s->Rsum, (N2*)s->invR, s->scale, s->wR,
             s->stats);
     rc = compact(s->rp, Mh, s->flags, s->cnt, s->scan_tmp, s->nzr, s->nzrp, s->zr, &s->stats->n_nzr,
                  &s->stats->n_zr, st);
@@ -380,7 +385,7 @@ int fold_typed(splitsart_system* s, cudaStream_t st) {
                                                                           s->cp, s->cnt, s->row, (Pair*)s->valT);
     if (Nh > 0)
         csc_sort_colsum_kernel<T><<<(unsigned)((Nh + 127) / 128), 128, 0, st>>>(
-            Nh, s->cp, s->row, (Pair*)s->valT, s->scale, s->Csum, (N2*)s->invC, s->stats);
+            Nh, s->cp, s->row, (Pair*)s->valT, s->scale, s->Csum, (N2*)s->invC, s->wC, s->stats);
     rc = compact(s->cp, Nh, s->flags, s->cnt, s->scan_tmp, s->nzc, s->nzcp, nullptr, &s->stats->n_nzc, nullptr, st);
     if (rc) return rc;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "fold launch");

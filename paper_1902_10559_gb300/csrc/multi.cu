@@ -33,8 +33,8 @@ struct MultiArgs {
     const int32_t* cp;
     const int32_t* row;
     const typename T::Pair* valT;
-    const typename T::Norm2* invR;
-    const typename T::Norm2* invC;
+    const typename T::KNorm2* invR;  // as applied (BF16/FP16: scale / R in FP32)
+    const typename T::KNorm2* invC;
     const float2* scale;
     const typename T::Vec2* p12;  // [nrhs][Mh]
     typename T::Vec2* f12;        // [nrhs][Nh]
@@ -52,7 +52,7 @@ template <class T, int RC, int RPW>
 __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
     using Acc = typename T::Acc;
     using V2 = typename T::Vec2;
-    using N2 = typename T::Norm2;
+    using N2 = typename T::KNorm2;
     using Pair = typename T::Pair;
     constexpr int LPR = 32 / (RC * RPW);  // lanes per (row, right-hand side)
     static_assert(LPR >= 1, "too many groups per warp");
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
 
     for (int k = 0;; ++k) {
         // ---- forward: RPW rows per warp, one lane group per (row, right-hand side) ----
-        double rrd = 0.0;  // this lane group's ||r||^2 over its rows, FP64
+        SqAcc<Acc> rr;  // this lane group's ||r||^2 over its rows
         for (int i0 = wib * RPW; i0 < Mh; i0 += nwarps * RPW) {
             const int i = i0 + rw;
             Acc s1 = 0, s2 = 0;
@@ -153,25 +153,18 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
             if (sub == 0 && i < Mh) {
                 const V2 p = s_p[i * RC + g];
                 const N2 ir = s_ir[i];
-                V2 u;
-                Acc r1, r2;
                 if constexpr (T::kQuant) {
                     const float2 sc = s_sc[i];
-                    r1 = p.x - s1 * sc.x;
-                    r2 = p.y - s2 * sc.y;
-                    u.x = (Acc)((double)r1 * ir.x * (double)sc.x);
-                    u.y = (Acc)((double)r2 * ir.y * (double)sc.y);
-                } else {
-                    r1 = p.x - s1;
-                    r2 = p.y - s2;
-                    u.x = r1 * ir.x;
-                    u.y = r2 * ir.y;
+                    s1 *= sc.x;
+                    s2 *= sc.y;
                 }
-                s_u[i * RC + g] = u;
-                rrd += (double)r1 * (double)r1 + (double)r2 * (double)r2;
+                const Acc r1 = p.x - s1, r2 = p.y - s2;
+                // For BF16/FP16, ir already holds the row scale (the codes are reused by the back-projection).
+                s_u[i * RC + g] = V2{r1 * ir.x, r2 * ir.y};
+                rr.add(r1, r2);
             }
         }
-        if (sub == 0) s_rr[wib][rw][g] = rrd;
+        if (sub == 0) s_rr[wib][rw][g] = rr.sum();
         __syncthreads();
         // ---- stop tests, one thread per right-hand side, fixed order ----
         const bool last = k >= a.max_iters;
@@ -210,13 +203,8 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
             if (sub == 0 && j < Nh && !s_done[g]) {
                 const N2 ic = s_ic[j];
                 V2 f = s_f[j * RC + g];
-                if constexpr (T::kQuant) {
-                    f.x += (Acc)((double)(lam * b1) * ic.x);
-                    f.y += (Acc)((double)(lam * b2) * ic.y);
-                } else {
-                    f.x += lam * b1 * ic.x;
-                    f.y += lam * b2 * ic.y;
-                }
+                f.x += lam * b1 * ic.x;
+                f.y += lam * b2 * ic.y;
                 s_f[j * RC + g] = f;
             }
         }
@@ -231,7 +219,7 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
 template <class T>
 size_t multi_smem_bytes(const splitsart_system* s, int S, int RC) {
     auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
-    const size_t pb = sizeof(typename T::Pair), nb = sizeof(typename T::Norm2), vb = sizeof(typename T::Vec2);
+    const size_t pb = sizeof(typename T::Pair), nb = sizeof(typename T::KNorm2), vb = sizeof(typename T::Vec2);
     return al(4 * (s->Mh + 1)) + al(4 * (size_t)S) + al(pb * S) + al(4 * (s->Nh + 1)) + al(4 * (size_t)S) +
            al(pb * S) + al(nb * s->Mh) + al(nb * s->Nh) + (T::kQuant ? al(8 * s->Mh) : 0) + 2 * al(vb * s->Mh * RC) +
            al(vb * s->Nh * RC);
@@ -264,8 +252,9 @@ int launch_multi(splitsart_system* s, int S, int nrhs, const void* p12, void* f1
     a.cp = s->cp;
     a.row = s->row;
     a.valT = (const typename T::Pair*)s->valT;
-    a.invR = (const typename T::Norm2*)s->invR;
-    a.invC = (const typename T::Norm2*)s->invC;
+    using KN2 = typename T::KNorm2;
+    a.invR = (const KN2*)(T::kQuant ? (const void*)s->wR : s->invR);
+    a.invC = (const KN2*)(T::kQuant ? (const void*)s->wC : s->invC);
     a.scale = s->scale;
     a.p12 = (const typename T::Vec2*)p12;
     a.f12 = (typename T::Vec2*)f12;

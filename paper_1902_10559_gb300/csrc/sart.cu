@@ -58,13 +58,13 @@ struct SartArgs {
     const typename T::Pair* __restrict__ val;
     const int32_t* __restrict__ row;
     const typename T::Pair* __restrict__ valT;
-    const typename T::Norm2* __restrict__ invR;
-    const typename T::Norm2* __restrict__ invC;
+    const typename T::KNorm2* __restrict__ invR;  // as applied (BF16/FP16: scale / R in FP32)
+    const typename T::KNorm2* __restrict__ invC;
     const float2* __restrict__ scale;
     const typename T::Vec2* __restrict__ p12;
     typename T::Vec2* f12;
     typename T::Vec2* u12;
-    double* partials;  // [2 * gridDim.x]: (rr, pp) per CTA
+    double* partials;  // [2 * gridDim.x]: (rr, pp) per CTA; pp is written once per launch
     LaunchCtl* ctl;
     SolveResultDev* result;
     const FoldStats* stats;
@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
     __shared__ int s_ct[kMaxTiles + 1];
     __shared__ int s_nrt, s_nct;
     __shared__ double s_red[2][32];
+    __shared__ double s_tpp;
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -189,21 +190,37 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
             if (nt < 0) atomicCAS(&a.ctl->err, 0, SPLITSART_ERR_ARG);
         }
     }
-    double ppz = 0.0;  // sum of p1^2 + p2^2 over this CTA's share of the empty rows
-    {
+    // ||p||^2 is fixed for the launch: this CTA's share of it over all rows
+    // (to partials[2b + 1]), and over the empty rows, whose residual is p.
+    double ppz = 0.0;  // meaningful in thread 0 only
+    if constexpr (!kBatch) {
         const long long G = gridDim.x, b = blockIdx.x;
         const int z0 = (int)(n_zr * b / G), z1 = (int)(n_zr * (b + 1) / G);
+        const long long Mall = kDirect ? a.direct_rows : (long long)n_nzr + n_zr;
+        const long long m0 = Mall * b / G, m1 = Mall * (b + 1) / G;
+        double tz = 0.0, ta = 0.0;
         for (int z = z0 + tid; z < z1; z += BD) {
             const V2 p = ldg(a.p12 + __ldg(a.zr + z));
-            ppz += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+            tz += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
         }
-        ppz = warp_sum(ppz);
-        if (lane == 0) s_red[0][wib] = ppz;
+        for (long long i = m0 + tid; i < m1; i += BD) {
+            const V2 p = ldg(a.p12 + i);
+            ta += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+        }
+        tz = warp_sum(tz);
+        ta = warp_sum(ta);
+        if (lane == 0) {
+            s_red[0][wib] = tz;
+            s_red[1][wib] = ta;
+        }
         __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < nwarps; ++w) t += s_red[0][w];
-            ppz = t;  // meaningful in thread 0 only
+        if (wib == 0) {
+            tz = warp_sum(lane < nwarps ? s_red[0][lane] : 0.0);
+            ta = warp_sum(lane < nwarps ? s_red[1][lane] : 0.0);
+            if (lane == 0) {
+                ppz = tz;
+                __stcg(a.partials + 2 * blockIdx.x + 1, ta);
+            }
         }
     }
     unsigned nbar = 0;
@@ -229,10 +246,14 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
     }
     if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     const int nrt = s_nrt, nct = s_nct;
+    if (!kBatch && wib == 0) {
+        const double t = grid_total(a.partials, gridDim.x, lane, 1);
+        if (lane == 0) s_tpp = t;  // read after later CTA barriers
+    }
 
     for (int k = 0;; ++k) {
         // ---- forward: r = p - A f, u = r / R, and the norm partials ----
-        double rr = 0.0, pp = 0.0;
+        SqAcc<Acc> rr;  // lane 0 of each warp: its rows' ||r||^2
         for (int t = 0; t < nrt; ++t) {
             const int qa = s_rt[t], qb = s_rt[t + 1];
             const int ea = __ldg(a.nzrp + qa), eb = __ldg(a.nzrp + qb);
@@ -267,7 +288,7 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
                 const int i = kDirect ? q : __ldg(a.nzr + q);
                 const int lo = __ldg(a.nzrp + q) - ea, hi = __ldg(a.nzrp + q + 1) - ea;
                 V2 p{};
-                typename T::Norm2 ir{};
+                typename T::KNorm2 ir{};
                 float2 sc{};
                 if (lane == 0) {
                     p = ldg(a.p12 + i);
@@ -299,39 +320,26 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
                         s2 *= sc.y;
                     }
                     const Acc r1 = p.x - s1, r2 = p.y - s2;
-                    V2 u;
-                    if constexpr (T::kQuant) {
-                        // The back-projection reuses the codes, so the row scale moves into u.
-                        u.x = (Acc)((double)r1 * ir.x * (double)sc.x);
-                        u.y = (Acc)((double)r2 * ir.y * (double)sc.y);
-                    } else {
-                        u.x = r1 * ir.x;
-                        u.y = r2 * ir.y;
-                    }
+                    // For BF16/FP16, ir already holds the row scale: the back-projection
+                    // reuses the codes, so the scale moves into u.
+                    const V2 u{r1 * ir.x, r2 * ir.y};
                     stcg(a.u12 + i, u);
                     if constexpr (kBatch) {
-                        __stcg(a.rr_row + i, (double)r1 * (double)r1 + (double)r2 * (double)r2);
+                        __stcg(a.rr_row + i, (double)(r1 * r1 + r2 * r2));
                     } else {
-                        rr += (double)r1 * (double)r1 + (double)r2 * (double)r2;
-                        pp += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+                        rr.add(r1, r2);
                     }
                 }
             }
             __syncthreads();  // prod is reused by the next tile
         }
-        if (lane == 0) {
-            s_red[0][wib] = rr;
-            s_red[1][wib] = pp;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double t0 = ppz, t1 = ppz;  // an empty row's residual is its p
-            for (int w = 0; w < nwarps; ++w) {
-                t0 += s_red[0][w];
-                t1 += s_red[1][w];
+        if constexpr (!kBatch) {
+            if (lane == 0) s_red[0][wib] = rr.sum();
+            __syncthreads();
+            if (wib == 0) {
+                const double t = warp_sum(lane < nwarps ? s_red[0][lane] : 0.0);
+                if (lane == 0) __stcg(a.partials + 2 * blockIdx.x, t + ppz);  // an empty row's residual is its p
             }
-            __stcg(a.partials + 2 * blockIdx.x, t0);
-            __stcg(a.partials + 2 * blockIdx.x + 1, t1);
         }
         if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
 
@@ -364,15 +372,11 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
         } else if (last || (k % a.check_every == 0)) {
             // ---- stop test: every CTA sums the partials in the same order ----
             if (wib == 0) {
-                double t0, t1;
-                grid_totals(a.partials, gridDim.x, lane, t0, t1);
-                if (lane == 0) {
-                    s_red[0][0] = t0;
-                    s_red[1][0] = t1;
-                }
+                const double t0 = grid_total(a.partials, gridDim.x, lane, 0);
+                if (lane == 0) s_red[0][0] = t0;
             }
             __syncthreads();
-            const double trr = s_red[0][0], tpp = s_red[1][0];
+            const double trr = s_red[0][0], tpp = s_tpp;
             const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
             if (last || rho <= a.tol) {
                 if (blockIdx.x == 0 && tid == 0) {
@@ -448,15 +452,10 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
                     if (sub == 0 && j >= 0) frozen = __ldcg(&a.sl_solve[slice_index(a.sl_cols, a.ns, j)].done) != 0;
                 }
                 if (sub == 0 && j >= 0 && !frozen) {
-                    const typename T::Norm2 ic = ldg(a.invC + j);
+                    const typename T::KNorm2 ic = ldg(a.invC + j);
                     V2 f = ldcg(a.f12 + j);
-                    if constexpr (T::kQuant) {
-                        f.x += (Acc)((double)(lam * b1) * ic.x);
-                        f.y += (Acc)((double)(lam * b2) * ic.y);
-                    } else {
-                        f.x += lam * b1 * ic.x;
-                        f.y += lam * b2 * ic.y;
-                    }
+                    f.x += lam * b1 * ic.x;
+                    f.y += lam * b2 * ic.y;
                     stcg(a.f12 + j, f);
                 }
             }
@@ -494,9 +493,9 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
 template <class T>
 struct ResidentBytes {
     static constexpr int kEntry = (int)sizeof(typename T::Pair) + 2;
-    static constexpr int kRow = 4 + 4 + (int)sizeof(typename T::Vec2) + (int)sizeof(typename T::Norm2) +
+    static constexpr int kRow = 4 + 4 + (int)sizeof(typename T::Vec2) + (int)sizeof(typename T::KNorm2) +
                                 (T::kQuant ? (int)sizeof(float2) : 0);
-    static constexpr int kCol = 4 + 4 + (int)sizeof(typename T::Norm2) + (int)sizeof(typename T::Vec2);
+    static constexpr int kCol = 4 + 4 + (int)sizeof(typename T::KNorm2) + (int)sizeof(typename T::Vec2);
     static constexpr int kThread = 0;
     static constexpr int kSlack = 12 * 16 + 16;  // alignment of 12 segments, plus the end pointers
     static constexpr int kChunk = sizeof(typename T::Vec2) == 16 ? 2 : 4;  // gathers in flight per lane and item
@@ -546,15 +545,17 @@ template <class T, int LPC>
 __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, int smem_bytes) {
     using Acc = typename T::Acc;
     using V2 = typename T::Vec2;
-    using N2 = typename T::Norm2;
+    using N2 = typename T::KNorm2;
     using Pair = typename T::Pair;
     using B = ResidentBytes<T>;
     constexpr int U = B::kChunk;           // gathers in flight per lane and item
     constexpr int kGroupsPerWarp = 32 / LPC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int2 s_rows, s_cols;
-    __shared__ double2 s_thr[512];
-    __shared__ double s_tot[2];
+    __shared__ double s_rrw[32];  // per warp: ||r||^2 of its rows
+    __shared__ double2 s_pw[32];  // per warp, once: ||p||^2 over the empty rows, and over all rows
+    __shared__ double s_tot[2];   // totals over the grid: ||r||^2 (per check), ||p||^2 (once)
+    __shared__ double s_ppz;      // this CTA's ||p||^2 over its share of the empty rows
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -638,17 +639,41 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
         c_f[q] = ldcg(a.f12 + j);
     }
     if (tid == 0) c_ptr[nc] = nbe;
-    double ppz = 0.0;  // this thread's share of sum(p1^2 + p2^2) over the empty rows
+    // ||p||^2 is fixed for the launch. This CTA's share over its empty rows
+    // (whose residual is p) and over all of its rows, summed once.
     {
         const long long G = gridDim.x, b = blockIdx.x;
         const int z0 = (int)(n_zr * b / G), z1 = (int)(n_zr * (b + 1) / G);
+        double tz = 0.0, ta = 0.0;
         for (int z = z0 + tid; z < z1; z += BD) {
             const V2 p = ldg(a.p12 + __ldg(a.zr + z));
-            ppz += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+            tz += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+        }
+        for (int q = tid; q < nr; q += BD) {
+            const V2 p = ldg(a.p12 + __ldg(a.nzr + q0 + q));
+            ta += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+        }
+        ta += tz;
+        tz = warp_sum(tz);
+        ta = warp_sum(ta);
+        if (lane == 0) s_pw[wib] = make_double2(tz, ta);
+        __syncthreads();
+        if (wib == 0) {
+            const double2 v = lane < nwarps ? s_pw[lane] : make_double2(0.0, 0.0);
+            const double t0 = warp_sum(v.x), t1 = warp_sum(v.y);
+            if (lane == 0) {
+                s_ppz = t0;
+                __stcg(a.partials + 2 * blockIdx.x + 1, t1);
+            }
         }
     }
     unsigned nbar = 0;
     if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+    if (wib == 0) {
+        const double t = grid_total(a.partials, gridDim.x, lane, 1);
+        if (lane == 0) s_tot[1] = t;  // read after later CTA barriers
+    }
+    const double ppz = s_ppz;
 
     // Gathers of one item's first U*W entries (lane-strided by W), and their use.
     auto issue = [&](const uint16_t* idx, const V2* src, int lo, int hi, int first, int W, V2 (&g)[U]) {
@@ -682,28 +707,20 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
 
     for (int k = 0;; ++k) {
         // ---- forward: r = p - A f, u = r / R, and the norm partials ----
-        double rr = ppz, pp = ppz;  // an empty row's residual is its p
+        SqAcc<Acc> rr;  // lane 0 of each warp: its rows' ||r||^2
         auto fin_row = [&](int q, Acc s1, Acc s2) {
             const V2 p = r_p[q];
             const N2 ir = r_ir[q];
-            V2 u;
             if constexpr (T::kQuant) {
                 const float2 sc = r_sc[q];
                 s1 *= sc.x;
                 s2 *= sc.y;
-                const Acc r1 = p.x - s1, r2 = p.y - s2;
-                // The back-projection reuses the codes, so the row scale moves into u.
-                u.x = (Acc)((double)r1 * ir.x * (double)sc.x);
-                u.y = (Acc)((double)r2 * ir.y * (double)sc.y);
-                rr += (double)r1 * (double)r1 + (double)r2 * (double)r2;
-            } else {
-                const Acc r1 = p.x - s1, r2 = p.y - s2;
-                u.x = r1 * ir.x;
-                u.y = r2 * ir.y;
-                rr += (double)r1 * (double)r1 + (double)r2 * (double)r2;
             }
-            pp += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
-            stcg(a.u12 + r_id[q], u);
+            const Acc r1 = p.x - s1, r2 = p.y - s2;
+            // For BF16/FP16, ir already holds the row scale: the back-projection
+            // reuses the codes, so the scale moves into u.
+            stcg(a.u12 + r_id[q], V2{r1 * ir.x, r2 * ir.y});
+            rr.add(r1, r2);
         };
         // Two rows per warp in flight: q and q + nwarps.
         for (int q = wib; q < nr; q += 2 * nwarps) {
@@ -727,22 +744,11 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
                 if (qb < nr) fin_row(qb, sB1, sB2);
             }
         }
-        // FP64 is scarce on this part: one warp sums the per-thread values.
-        s_thr[tid] = make_double2(rr, pp);
+        if (lane == 0) s_rrw[wib] = rr.sum();
         __syncthreads();
         if (wib == 0) {
-            double t0 = 0.0, t1 = 0.0;
-            for (int t = lane; t < BD; t += 32) {
-                const double2 v = s_thr[t];
-                t0 += v.x;
-                t1 += v.y;
-            }
-            t0 = warp_sum(t0);
-            t1 = warp_sum(t1);
-            if (lane == 0) {
-                __stcg(a.partials + 2 * blockIdx.x, t0);
-                __stcg(a.partials + 2 * blockIdx.x + 1, t1);
-            }
+            const double t = warp_sum(lane < nwarps ? s_rrw[lane] : 0.0);
+            if (lane == 0) __stcg(a.partials + 2 * blockIdx.x, t + ppz);  // an empty row's residual is its p
         }
         if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
 
@@ -752,13 +758,8 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
         auto fin_col = [&](int q, Acc b1, Acc b2) {
             const N2 ic = c_ic[q];
             V2 f = c_f[q];
-            if constexpr (T::kQuant) {
-                f.x += (Acc)((double)(lam * b1) * ic.x);
-                f.y += (Acc)((double)(lam * b2) * ic.y);
-            } else {
-                f.x += lam * b1 * ic.x;
-                f.y += lam * b2 * ic.y;
-            }
+            f.x += lam * b1 * ic.x;
+            f.y += lam * b2 * ic.y;
             c_f[q] = f;
             stcg(a.f12 + c_id[q], f);
         };
@@ -775,12 +776,8 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
                 first_pass = false;
                 if (check) {  // uniform over the CTA
                     if (wib == 0) {
-                        double t0, t1;
-                        grid_totals(a.partials, gridDim.x, lane, t0, t1);
-                        if (lane == 0) {
-                            s_tot[0] = t0;
-                            s_tot[1] = t1;
-                        }
+                        const double t0 = grid_total(a.partials, gridDim.x, lane, 0);
+                        if (lane == 0) s_tot[0] = t0;
                     }
                     __syncthreads();
                     const double trr = s_tot[0], tpp = s_tot[1];
@@ -833,8 +830,9 @@ void fill_args(SartArgs<T>& a, splitsart_system* s, const void* p12, void* f12, 
     a.val = (const typename T::Pair*)s->val;
     a.row = s->row;
     a.valT = (const typename T::Pair*)s->valT;
-    a.invR = (const typename T::Norm2*)s->invR;
-    a.invC = (const typename T::Norm2*)s->invC;
+    using KN2 = typename T::KNorm2;
+    a.invR = (const KN2*)(T::kQuant ? (const void*)s->wR : s->invR);
+    a.invC = (const KN2*)(T::kQuant ? (const void*)s->wC : s->invC);
     a.scale = s->scale;
     a.p12 = (const typename T::Vec2*)p12;
     a.f12 = (typename T::Vec2*)f12;

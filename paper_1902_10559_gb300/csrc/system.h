@@ -91,6 +91,8 @@ struct splitsart_system {
     void* invR = nullptr;     // Mh pairs
     void* invC = nullptr;     // Nh pairs
     float2* scale = nullptr;  // Mh (BF16/F16 only)
+    float2* wR = nullptr;     // Mh (BF16/F16 only): fl32(scale / R), as the iteration applies it
+    float2* wC = nullptr;     // Nh (BF16/F16 only): fl32(1 / C)
 
     // Compacted index lists (entries of empty rows/columns are skipped by the solve).
     int32_t* nzr = nullptr;   // rows with entries, increasing (n_nzr)

@@ -151,7 +151,40 @@ class WarmStart:
             self.cnn.forward(x[a:b].contiguous(), y[a:b])
         return y
 
-    # ---- 3./4. comparison to rho <= tol ----
+    # ---- 3./4. warm-started and plain solves to rho <= tol ----
+    def solve_plain(self, p12, tol, max_iters):
+        """Plain split-SART from zero. Returns (f12, info)."""
+        import torch
+        f = torch.zeros(p12.shape[0], self.g.N // 2, 2, device=self.dev)
+        return f, self.solve(p12, f, max_iters, tol)
+
+    def solve_warm(self, p12, tol, max_iters):
+        """5 iterations, network, fold, fallback, continue. Returns (f12, info_early, info_rest, picked).
+
+        A right-hand side that met tol within the first 5 iterations has
+        stopped there; the continuation then returns it unchanged with 0
+        further iterations.
+        """
+        import torch
+        n = p12.shape[0]
+        f_warm = torch.zeros(n, self.g.N // 2, 2, device=self.dev)
+        info_early = self.solve(p12, f_warm, EARLY_ITERS, tol)
+        guess = self.fold_image(self.predict(self.recombine(f_warm)))
+        info_guess = self.solve(p12, guess, 0)  # rho of the guess
+        info_zero = self.solve(p12, torch.zeros_like(guess), 0)  # rho of a zero start (1, or 0 if p = 0)
+        picked = torch.zeros(n, dtype=torch.int32, device=self.dev)
+        ss.pick_start(self.system, guess, info_guess, info_zero, f_warm, picked)
+        info_rest = self.solve(p12, f_warm, max_iters - EARLY_ITERS, tol)
+        self._last_guess_info = info_guess
+        return f_warm, info_early, info_rest, picked
+
+    @staticmethod
+    def warm_counts(early, rest, tol):
+        """Per right-hand side: total iterations and final rho of the warm-started solve."""
+        its = np.array([e["iters"] if e["rho"] <= tol else EARLY_ITERS + r["iters"] for e, r in zip(early, rest)])
+        rho = np.array([e["rho"] if e["rho"] <= tol else r["rho"] for e, r in zip(early, rest)])
+        return its, rho
+
     def compare(self, seeds, tol=1e-3, max_iters=20000):
         """Plain split-SART from zero vs the warm start, on the seeded phantoms.
 
@@ -162,37 +195,24 @@ class WarmStart:
         p12 = self.fold_rhs(self.project(truth))
         n = len(seeds)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        # Plain.
-        f_plain = torch.zeros(n, self.g.N // 2, 2, device=self.dev)
         torch.cuda.synchronize()
         ev[0].record()
-        info_plain = self.solve(p12, f_plain, max_iters, tol)
+        _, info_plain = self.solve_plain(p12, tol, max_iters)
         ev[1].record()
-        # Warm: 5 iterations, network, fold, fallback, continue.
-        f_warm = torch.zeros(n, self.g.N // 2, 2, device=self.dev)
         ev[2].record()
-        info_early = self.solve(p12, f_warm, EARLY_ITERS, tol)
-        guess = self.fold_image(self.predict(self.recombine(f_warm)))
-        info_guess = self.solve(p12, guess, 0)  # rho of the guess
-        info_zero = self.solve(p12, torch.zeros_like(guess), 0)  # rho of a zero start (1, or 0 if p = 0)
-        picked = torch.zeros(n, dtype=torch.int32, device=self.dev)
-        ss.pick_start(self.system, guess, info_guess, info_zero, f_warm, picked)
-        info_rest = self.solve(p12, f_warm, max_iters - EARLY_ITERS, tol)
+        _, info_early, info_rest, picked = self.solve_warm(p12, tol, max_iters)
         ev[3].record()
         torch.cuda.synchronize()
-        it_plain = np.array([i["iters"] for i in ss.read_infos(info_plain, n)])
+        plain = ss.read_infos(info_plain, n)
         early = ss.read_infos(info_early, n)
         rest = ss.read_infos(info_rest, n)
-        # A right-hand side that already met tol within the first 5 iterations stops there.
-        it_warm = np.array([e["iters"] if e["rho"] <= tol else EARLY_ITERS + r["iters"] for e, r in zip(early, rest)])
-        rho_plain = np.array([i["rho"] for i in ss.read_infos(info_plain, n)])
-        rho_warm = np.array([e["rho"] if e["rho"] <= tol else r["rho"] for e, r in zip(early, rest)])
+        it_warm, rho_warm = self.warm_counts(early, rest, tol)
         return {
             "n": n, "tol": tol,
-            "iters_plain": it_plain, "iters_warm": it_warm,
-            "rho_plain": rho_plain, "rho_warm": rho_warm,
+            "iters_plain": np.array([i["iters"] for i in plain]), "iters_warm": it_warm,
+            "rho_plain": np.array([i["rho"] for i in plain]), "rho_warm": rho_warm,
             "ms_plain": ev[0].elapsed_time(ev[1]), "ms_warm": ev[2].elapsed_time(ev[3]),
             "warm_kept": float(picked.float().mean().item()),
             "rho_early": np.array([e["rho"] for e in early]),
-            "rho_guess": np.array([i["rho"] for i in ss.read_infos(info_guess, n)]),
+            "rho_guess": np.array([i["rho"] for i in ss.read_infos(self._last_guess_info, n)]),
         }
