@@ -4,8 +4,9 @@ Each tunable is timed with a short solve and the fastest is kept. Choices are
 cached per (device, storage type, problem class) in a JSON file:
 $SPLITSART_TUNE_CACHE, or ~/.cache/splitsart/tune.json.
 
-- Persistent solve: kernel (shared-memory resident or streaming), tile
-  entries per CTA, lanes per column in the back-projection, threads per CTA.
+- Persistent solve: kernel (shared-memory resident, tile streaming, row
+  streaming through registers, or per-warp bulk-staged streaming), tile entries per CTA, lanes per column in the back-projection,
+  threads per CTA.
 - Multi-right-hand-side solve: right-hand sides per CTA, threads per CTA.
 
 The tuner only chooses among launch shapes of the same arithmetic, so every
@@ -83,6 +84,10 @@ def solve_candidates(system: ss.System) -> list[dict]:
         for lpc in (4, 8, 16):
             for bt in (256, 384, 512):
                 out.append({"kernel": 2, "lanes_per_col": lpc, "block_threads": bt, "tile_entries": 0})
+    for kern, bts in ((4, (256, 384)), (3, (256, 512))):
+        for lpc in (4, 8, 16):
+            for bt in bts:
+                out.append({"kernel": kern, "lanes_per_col": lpc, "block_threads": bt, "tile_entries": 0})
     for lpc in (4, 8, 16):
         for te in (4096, 8192, 12288):
             if system.dtype == ss.F64 and te > 8192:

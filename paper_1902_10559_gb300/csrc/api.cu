@@ -462,7 +462,7 @@ extern "C" int splitsart_solve(splitsart_system* s, const void* p12, void* f12, 
     if ((s->Mh > 0 && !p12) || (s->Nh > 0 && !f12)) return fail(SPLITSART_ERR_ARG, "solve: NULL vector");
     if (o->max_iters < 0 || o->max_iters > 500000)
         return fail(SPLITSART_ERR_ARG, "solve: max_iters must be in [0, 500000]");
-    if (o->kernel < 0 || o->kernel > 2) return fail(SPLITSART_ERR_ARG, "solve: kernel must be 0, 1 or 2");
+    if (o->kernel < 0 || o->kernel > 4) return fail(SPLITSART_ERR_ARG, "solve: kernel must be 0, 1, 2, 3 or 4");
     if (o->tile_entries != 0 && (o->tile_entries % 1024 != 0 || o->tile_entries < 1024 || o->tile_entries > 16384))
         return fail(SPLITSART_ERR_ARG, "solve: tile_entries must be 0 or a multiple of 1024 in [1024, 16384]");
     if (!(o->lambda > 0.0) || !std::isfinite(o->lambda)) return fail(SPLITSART_ERR_ARG, "solve: lambda must be > 0");

@@ -153,8 +153,9 @@ __device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_c
 struct LaunchCtl {
     unsigned bar_count;
     unsigned bar_gen;
-    int err;       // 0, or a SPLITSART_ERR_* code
-    int err_where; // barrier index at which a wait ran out
+    int err;          // 0, or a SPLITSART_ERR_* code
+    int err_where;    // barrier index at which a wait ran out
+    unsigned work[2]; // work counters of dynamically scheduled passes (forward, back)
 };
 
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).
@@ -200,6 +201,55 @@ __device__ __forceinline__ bool grid_sync(LaunchCtl* ctl, unsigned target, unsig
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (global -> shared) completed on an mbarrier.
+// Both addresses must be 16-byte aligned and the size a multiple of 16.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// Wait for the completion of the given phase parity, with a wall-clock limit
+// and a spin cap. Returns false if either runs out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned long long timeout_ns) {
+    const uint32_t addr = smem_addr(bar);
+    const unsigned long long t0 = global_ns();
+    const unsigned long long max_spins = timeout_ns / 16ull + (1ull << 20);
+    for (unsigned long long spins = 0;; ++spins) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (spins > max_spins || global_ns() - t0 > timeout_ns) return false;
+    }
+}
+// Order this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy (bulk copy) writes to it.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
 }
 
 // One warp: the sum of partials[2b + which] over b < nparts, in a fixed

@@ -36,6 +36,7 @@
 #include <cmath>
 #include <cstdio>
 #include <mutex>
+#include <type_traits>
 
 #include "device_common.cuh"
 #include "system.h"
@@ -520,12 +521,18 @@ __device__ __forceinline__ int warp_lower_bound_w(const int32_t* ptr, int lo, in
 }
 
 // One warp: this CTA's range [q0, q1) of [0, n), balanced by WE*entries + WR*items.
-__device__ __forceinline__ int2 resident_range(const int32_t* ptr, int n, int WE, int WR, int lane) {
+// One warp: part `part` of `nparts` of [0, n), balanced by WE*entries + WR*items.
+__device__ __forceinline__ int2 part_range(const int32_t* ptr, int n, int WE, int WR, long long part, long long nparts,
+                                           int lane) {
     const long long total = (long long)WE * __ldg(ptr + n) + (long long)WR * n;
-    const long long G = gridDim.x, b = blockIdx.x;
-    const int q0 = warp_lower_bound_w(ptr, 0, n, total * b / G, WE, WR, lane);
-    const int q1 = (b == G - 1) ? n : warp_lower_bound_w(ptr, 0, n, total * (b + 1) / G, WE, WR, lane);
+    const int q0 = warp_lower_bound_w(ptr, 0, n, total * part / nparts, WE, WR, lane);
+    const int q1 =
+        (part == nparts - 1) ? n : warp_lower_bound_w(ptr, 0, n, total * (part + 1) / nparts, WE, WR, lane);
     return make_int2(q0, q1);
+}
+
+__device__ __forceinline__ int2 resident_range(const int32_t* ptr, int n, int WE, int WR, int lane) {
+    return part_range(ptr, n, WE, WR, blockIdx.x, gridDim.x, lane);
 }
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -813,6 +820,717 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
     }
 }
 
+// ---------------------------------------------------------------------------
+// Row-streaming variant, for systems far larger than on-chip memory (the
+// batch of slices).
+//
+// The matrix is streamed from HBM once per pass, so the kernel must keep
+// enough loads in flight to cover DRAM latency. It has no CTA barriers
+// inside a pass:
+// - Work is scheduled dynamically. A warp takes the next chunk of 16
+//   non-empty rows (or 8 x 32/LPC non-empty columns) from a global counter,
+//   fetched one chunk ahead, so no warp waits at the pass's end for a slow
+//   static share. Chunks go out in order, so the warps of the grid work on
+//   neighbouring rows and the gathered vector stays hot in L2.
+// - Within a chunk a warp takes two adjacent rows at a time. Each lane first
+//   issues the index and value loads of up to U entries of both rows, then
+//   the U gathers, then the products; a row longer than 32 U entries
+//   continues in further rounds.
+// - The back-projection is the same over the CSC with LPC lanes per column
+//   and two groups of columns per warp.
+// Matrix loads use the streaming cache hint (read once per pass). Per-row
+// sums use the same lane-strided order and shuffle tree as the other
+// kernels, so f does not depend on the grid or the schedule. The FP32 group
+// sums of ||r||^2 do, so rho may differ in its last bits between runs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ldcs(const int32_t* p) { return __ldcs(p); }
+__device__ __forceinline__ float2 ldcs(const float2* p) { return __ldcs(p); }
+__device__ __forceinline__ double2 ldcs(const double2* p) { return __ldcs(p); }
+__device__ __forceinline__ __nv_bfloat162 ldcs(const __nv_bfloat162* p) {
+    unsigned v = __ldcs(reinterpret_cast<const unsigned*>(p));
+    return *reinterpret_cast<__nv_bfloat162*>(&v);
+}
+__device__ __forceinline__ __half2 ldcs(const __half2* p) {
+    unsigned v = __ldcs(reinterpret_cast<const unsigned*>(p));
+    return *reinterpret_cast<__half2*>(&v);
+}
+
+template <class T, int LPC, bool kBatch>
+__global__ void __launch_bounds__(512, 1) sart_rows_kernel(SartArgs<T> a) {
+    using Acc = typename T::Acc;
+    using V2 = typename T::Vec2;
+    using N2 = typename T::KNorm2;
+    using Pair = typename T::Pair;
+    constexpr int U = sizeof(V2) == 16 ? 2 : 4;  // entries in flight per lane and row
+    constexpr int kGroupsPerWarp = 32 / LPC;
+    constexpr int kRowChunk = 16;  // rows per scheduled chunk
+    __shared__ double s_red[2][32];
+    __shared__ double s_tpp;
+
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nwarps = blockDim.x >> 5, BD = blockDim.x;
+    const int sub = lane % LPC;
+    const Acc lam = (Acc)a.lambda;
+    const int n_nzr = a.stats->n_nzr, n_nzc = a.stats->n_nzc, n_zr = a.stats->n_zr;
+
+    // ---- launch prologue: the fixed ||p||^2 terms ----
+    double ppz = 0.0;  // meaningful in thread 0 only
+    const int gw = blockIdx.x * nwarps + wib, nw_grid = gridDim.x * nwarps;
+    if constexpr (kBatch) {
+        // Empty rows keep residual p; each slice's ||p||^2 is summed once.
+        for (int z = blockIdx.x * BD + tid; z < n_zr; z += gridDim.x * BD) {
+            const int i = __ldg(a.zr + z);
+            const V2 p = ldg(a.p12 + i);
+            a.rr_row[i] = (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+        }
+        for (int sl = gw; sl < a.ns; sl += nw_grid) {
+            double t = 0.0;
+            for (long long i = __ldg(a.sl_rows + sl) + lane; i < __ldg(a.sl_rows + sl + 1); i += 32) {
+                const V2 p = ldg(a.p12 + i);
+                t += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+            }
+            t = warp_sum(t);
+            if (lane == 0) a.sl_solve[sl] = SliceSolve{-1, 0, 0.0, 0.0, t};
+        }
+    } else {
+        const long long G = gridDim.x, b = blockIdx.x;
+        const int z0 = (int)(n_zr * b / G), z1 = (int)(n_zr * (b + 1) / G);
+        const long long Mall = (long long)n_nzr + n_zr;
+        const long long m0 = Mall * b / G, m1 = Mall * (b + 1) / G;
+        double tz = 0.0, ta = 0.0;
+        for (int z = z0 + tid; z < z1; z += BD) {
+            const V2 p = ldg(a.p12 + __ldg(a.zr + z));
+            tz += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+        }
+        for (long long i = m0 + tid; i < m1; i += BD) {
+            const V2 p = ldg(a.p12 + i);
+            ta += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+        }
+        tz = warp_sum(tz);
+        ta = warp_sum(ta);
+        if (lane == 0) {
+            s_red[0][wib] = tz;
+            s_red[1][wib] = ta;
+        }
+        __syncthreads();
+        if (wib == 0) {
+            tz = warp_sum(lane < nwarps ? s_red[0][lane] : 0.0);
+            ta = warp_sum(lane < nwarps ? s_red[1][lane] : 0.0);
+            if (lane == 0) {
+                ppz = tz;
+                __stcg(a.partials + 2 * blockIdx.x + 1, ta);
+            }
+        }
+    }
+    unsigned nbar = 0;
+    if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+    if (!kBatch && wib == 0) {
+        const double t = grid_total(a.partials, gridDim.x, lane, 1);
+        if (lane == 0) s_tpp = t;  // read after later CTA barriers
+    }
+    // Loads of up to U entries of one item (lane-strided by W), then their gathers, then the products.
+    auto issue = [&](const int32_t* idx, const Pair* vals, int lo, int hi, int first, int W, int (&ix)[U],
+                     Pair (&v)[U]) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = lo + first + u * W;
+            if (e < hi) {
+                ix[u] = ldcs(idx + e);
+                v[u] = ldcs(vals + e);
+            }
+        }
+    };
+    auto gather = [&](const V2* src, int lo, int hi, int first, int W, const int (&ix)[U], V2 (&g)[U]) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = lo + first + u * W;
+            if (e < hi) g[u] = ldca(src + ix[u]);
+        }
+    };
+    auto consume = [&](int lo, int hi, int first, int W, const Pair (&v)[U], const V2 (&g)[U], Acc& s1, Acc& s2) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = lo + first + u * W;
+            if (e < hi) {
+                Acc v1, v2;
+                T::decode(v[u], v1, v2);
+                s1 += v1 * g[u].x;
+                s2 += v2 * g[u].y;
+            }
+        }
+    };
+    // Two items at once, all rounds: sums (A1, A2) of item A and of item B.
+    auto two_items = [&](const int32_t* idx, const Pair* vals, const V2* src, int loA, int hiA, int loB, int hiB,
+                         int first, int W, Acc& sA1, Acc& sA2, Acc& sB1, Acc& sB2) {
+        const int nA = hiA - loA, nB = hiB - loB, n = nA > nB ? nA : nB;
+        for (int base = first; base - first < n; base += U * W) {
+            int ixA[U], ixB[U];
+            Pair vA[U], vB[U];
+            V2 gA[U], gB[U];
+            issue(idx, vals, loA, hiA, base, W, ixA, vA);
+            issue(idx, vals, loB, hiB, base, W, ixB, vB);
+            gather(src, loA, hiA, base, W, ixA, gA);
+            gather(src, loB, hiB, base, W, ixB, gB);
+            consume(loA, hiA, base, W, vA, gA, sA1, sA2);
+            consume(loB, hiB, base, W, vB, gB, sB1, sB2);
+        }
+    };
+
+    for (int k = 0;; ++k) {
+        // ---- forward: r = p - A f, u = r / R, and the norm partials ----
+        SqAcc<Acc> rr;  // lane 0 of each warp: its rows' ||r||^2
+        auto fin_row = [&](int q, Acc s1, Acc s2) {
+            const int i = __ldg(a.nzr + q);
+            const V2 p = ldg(a.p12 + i);
+            const N2 ir = ldg(a.invR + i);
+            if constexpr (T::kQuant) {
+                const float2 sc = ldg(a.scale + i);
+                s1 *= sc.x;
+                s2 *= sc.y;
+            }
+            const Acc r1 = p.x - s1, r2 = p.y - s2;
+            // For BF16/FP16, ir already holds the row scale: the back-projection
+            // reuses the codes, so the scale moves into u.
+            stcg(a.u12 + i, V2{r1 * ir.x, r2 * ir.y});
+            if constexpr (kBatch) __stcg(a.rr_row + i, (double)(r1 * r1 + r2 * r2));
+            else rr.add(r1, r2);
+        };
+        if (blockIdx.x == 0 && tid == 0) a.ctl->work[1] = 0;  // the back pass's counter, idle until the barrier
+        int grab = 0;  // lane 0: the next chunk, fetched one chunk ahead
+        if (lane == 0) grab = atomicAdd(&a.ctl->work[0], 1u);
+        for (int chunk = __shfl_sync(0xffffffffu, grab, 0); chunk < (n_nzr + kRowChunk - 1) / kRowChunk;
+             chunk = __shfl_sync(0xffffffffu, grab, 0)) {
+            if (lane == 0) grab = atomicAdd(&a.ctl->work[0], 1u);
+            const int q1 = min((chunk + 1) * kRowChunk, n_nzr);
+            for (int q = chunk * kRowChunk; q < q1; q += 2) {
+                const bool hasB = q + 1 < q1;
+                const int loA = __ldg(a.nzrp + q), hiA = __ldg(a.nzrp + q + 1);
+                const int hiB = hasB ? __ldg(a.nzrp + q + 2) : hiA;
+                Acc sA1 = 0, sA2 = 0, sB1 = 0, sB2 = 0;
+                two_items(a.col, a.val, a.f12, loA, hiA, hiA, hiB, lane, 32, sA1, sA2, sB1, sB2);
+                sA1 = warp_sum(sA1);
+                sA2 = warp_sum(sA2);
+                sB1 = warp_sum(sB1);
+                sB2 = warp_sum(sB2);
+                if (lane == 0) {
+                    fin_row(q, sA1, sA2);
+                    if (hasB) fin_row(q + 1, sB1, sB2);
+                }
+            }
+        }
+        if constexpr (!kBatch) {
+            if (lane == 0) s_red[0][wib] = rr.sum();
+            __syncthreads();
+            if (wib == 0) {
+                const double t = warp_sum(lane < nwarps ? s_red[0][lane] : 0.0);
+                if (lane == 0) __stcg(a.partials + 2 * blockIdx.x, t + ppz);  // an empty row's residual is its p
+            }
+        }
+        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+
+        const bool last = (k >= a.max_iters);
+        if constexpr (kBatch) {
+            // ---- per-slice stop tests: one warp per slice, fixed order ----
+            if (last || (k % a.check_every == 0)) {
+                for (int sl = gw; sl < a.ns; sl += nw_grid) {
+                    if (__ldcg(&a.sl_solve[sl].done)) continue;
+                    const double trr = warp_sum_range(a.rr_row, __ldg(a.sl_rows + sl), __ldg(a.sl_rows + sl + 1), lane);
+                    const double tpp = __ldcg(&a.sl_solve[sl].pp);
+                    const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
+                    if (lane == 0 && (last || rho <= a.tol)) {
+                        a.sl_solve[sl] = SliceSolve{k, 1, rho, trr, tpp};
+                        atomicAdd(a.ndone, 1);
+                    }
+                }
+            }
+            if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+            if (ld_volatile(a.ndone) >= a.ns) {
+                if (blockIdx.x == 0 && tid == 0) {
+                    a.result->iters = k;
+                    a.result->status = SPLITSART_OK;
+                    a.result->rho = 0.0;
+                    a.result->rr = 0.0;
+                    a.result->pp = 0.0;
+                }
+                return;
+            }
+        } else if (last || (k % a.check_every == 0)) {
+            // ---- stop test: every CTA sums the partials in the same order ----
+            if (wib == 0) {
+                const double t0 = grid_total(a.partials, gridDim.x, lane, 0);
+                if (lane == 0) s_red[0][0] = t0;
+            }
+            __syncthreads();
+            const double trr = s_red[0][0], tpp = s_tpp;
+            const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
+            if (last || rho <= a.tol) {
+                if (blockIdx.x == 0 && tid == 0) {
+                    a.result->iters = k;
+                    a.result->status = SPLITSART_OK;
+                    a.result->rho = rho;
+                    a.result->rr = trr;
+                    a.result->pp = tpp;
+                }
+                return;
+            }
+        }
+
+        // ---- back-projection and update: f += lambda (A^T u) / C ----
+        // A lane's columns increase (chunks are handed out in order), so its
+        // slice is found by walking forward.
+        int sl = 0;
+        auto fin_col = [&](int q, Acc b1, Acc b2) {
+            const int j = __ldg(a.nzc + q);
+            if constexpr (kBatch) {
+                while (j >= __ldg(a.sl_cols + sl + 1)) ++sl;
+                if (__ldcg(&a.sl_solve[sl].done)) return;  // the slice has stopped: keep its returned iterate
+            }
+            const N2 ic = ldg(a.invC + j);
+            V2 f = ldcg(a.f12 + j);
+            f.x += lam * b1 * ic.x;
+            f.y += lam * b2 * ic.y;
+            stcg(a.f12 + j, f);
+        };
+        if (blockIdx.x == 0 && tid == 0) a.ctl->work[0] = 0;  // the forward pass's counter, idle until the barrier
+        constexpr int kColChunk = 4 * 2 * kGroupsPerWarp;
+        if (lane == 0) grab = atomicAdd(&a.ctl->work[1], 1u);
+        for (int chunk = __shfl_sync(0xffffffffu, grab, 0); chunk < (n_nzc + kColChunk - 1) / kColChunk;
+             chunk = __shfl_sync(0xffffffffu, grab, 0)) {
+            if (lane == 0) grab = atomicAdd(&a.ctl->work[1], 1u);
+            const int c1 = min((chunk + 1) * kColChunk, n_nzc);
+            // Warp-uniform loop over pairs of column groups, so every lane reaches the shuffles.
+            for (int g0 = chunk * kColChunk; g0 < c1; g0 += 2 * kGroupsPerWarp) {
+                const int qA = g0 + lane / LPC, qB = qA + kGroupsPerWarp;
+                const int loA = qA < c1 ? __ldg(a.nzcp + qA) : 0, hiA = qA < c1 ? __ldg(a.nzcp + qA + 1) : 0;
+                const int loB = qB < c1 ? __ldg(a.nzcp + qB) : 0, hiB = qB < c1 ? __ldg(a.nzcp + qB + 1) : 0;
+                Acc bA1 = 0, bA2 = 0, bB1 = 0, bB2 = 0;
+                two_items(a.row, a.valT, a.u12, loA, hiA, loB, hiB, sub, LPC, bA1, bA2, bB1, bB2);
+                bA1 = warp_sum(bA1, LPC);
+                bA2 = warp_sum(bA2, LPC);
+                bB1 = warp_sum(bB1, LPC);
+                bB2 = warp_sum(bB2, LPC);
+                if (sub == 0) {
+                    if (qA < c1) fin_col(qA, bA1, bA2);
+                    if (qB < c1) fin_col(qB, bB1, bB2);
+                }
+            }
+        }
+        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bulk-staged streaming, for systems far larger than on-chip memory.
+//
+// Every warp of the grid owns a contiguous range of non-empty rows and one
+// of non-empty columns, balanced by bytes. It walks each range in jobs of
+// two rows (forward) or 2 x 32/LPC columns (back).
+// - A job's indices and values are staged into one of the warp's two
+//   shared-memory slots by bulk asynchronous copies (cp.async.bulk),
+//   completed on the slot's mbarrier.
+// - The copy of job j + 1 is issued before job j is processed, and the
+//   pointers and metadata (p, 1/R and the row scale; or f and 1/C) of later
+//   jobs load meanwhile. The matrix stream therefore never waits for the
+//   warp's gathers, and registers hold only the gathers in flight.
+// - A job larger than a slot is read straight from global memory.
+// Warps never wait for one another inside a pass: the only CTA-wide
+// synchronisation is the grid barrier between passes. Each row and column
+// sum has the same lane-strided order and shuffle tree as in the other
+// kernels.
+// ---------------------------------------------------------------------------
+template <class T, int LPC, bool kBatch>
+__global__ void __launch_bounds__(384, 1) sart_bulk_kernel(SartArgs<T> a, int te) {
+    using Acc = typename T::Acc;
+    using V2 = typename T::Vec2;
+    using N2 = typename T::KNorm2;
+    using Pair = typename T::Pair;
+    // Gathers in flight per lane and item: for staged jobs, and for jobs read from global memory.
+    constexpr std::integral_constant<int, sizeof(V2) == 16 ? 2 : 8> kUS{};
+    constexpr std::integral_constant<int, 2> kUD{};
+    constexpr int kEB = 4 + (int)sizeof(Pair);  // staged bytes per entry
+    constexpr int GPW = 32 / LPC;                // column groups per warp
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t s_bar[16][2];
+    __shared__ double s_red[2][32];
+    __shared__ double s_tpp;
+
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nwarps = blockDim.x >> 5, BD = blockDim.x;
+    const int sub = lane % LPC;
+    const Acc lam = (Acc)a.lambda;
+    const int n_nzr = a.stats->n_nzr, n_nzc = a.stats->n_nzc, n_zr = a.stats->n_zr;
+    const int cap = te + 8;  // entries per slot: a tile plus the 16-byte alignment of both ends
+    unsigned char* wslots = smem_raw + (size_t)wib * 2 * cap * kEB;
+    uint64_t* bar = s_bar[wib];
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    unsigned phase = 0;     // bit s: parity of slot s's next completion
+    unsigned inflight = 0;  // bit s: a copy into slot s was issued and not yet waited for
+
+    // ---- launch prologue: ranges, and the fixed ||p||^2 terms ----
+    const int gw = blockIdx.x * nwarps + wib, nw_grid = gridDim.x * nwarps;
+    const int2 rrange = part_range(a.nzrp, n_nzr, 12, 32, gw, nw_grid, lane);
+    const int2 crange = part_range(a.nzcp, n_nzc, 12, 32, gw, nw_grid, lane);
+    double ppz = 0.0;  // meaningful in thread 0 only
+    if constexpr (kBatch) {
+        for (int z = blockIdx.x * BD + tid; z < n_zr; z += gridDim.x * BD) {
+            const int i = __ldg(a.zr + z);
+            const V2 p = ldg(a.p12 + i);
+            a.rr_row[i] = (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+        }
+        for (int sl = gw; sl < a.ns; sl += nw_grid) {
+            double t = 0.0;
+            for (long long i = __ldg(a.sl_rows + sl) + lane; i < __ldg(a.sl_rows + sl + 1); i += 32) {
+                const V2 p = ldg(a.p12 + i);
+                t += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+            }
+            t = warp_sum(t);
+            if (lane == 0) a.sl_solve[sl] = SliceSolve{-1, 0, 0.0, 0.0, t};
+        }
+    } else {
+        const long long G = gridDim.x, b = blockIdx.x;
+        const int z0 = (int)(n_zr * b / G), z1 = (int)(n_zr * (b + 1) / G);
+        const long long Mall = (long long)n_nzr + n_zr;
+        const long long m0 = Mall * b / G, m1 = Mall * (b + 1) / G;
+        double tz = 0.0, ta = 0.0;
+        for (int z = z0 + tid; z < z1; z += BD) {
+            const V2 p = ldg(a.p12 + __ldg(a.zr + z));
+            tz += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+        }
+        for (long long i = m0 + tid; i < m1; i += BD) {
+            const V2 p = ldg(a.p12 + i);
+            ta += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+        }
+        tz = warp_sum(tz);
+        ta = warp_sum(ta);
+        if (lane == 0) {
+            s_red[0][wib] = tz;
+            s_red[1][wib] = ta;
+        }
+        __syncthreads();
+        if (wib == 0) {
+            tz = warp_sum(lane < nwarps ? s_red[0][lane] : 0.0);
+            ta = warp_sum(lane < nwarps ? s_red[1][lane] : 0.0);
+            if (lane == 0) {
+                ppz = tz;
+                __stcg(a.partials + 2 * blockIdx.x + 1, ta);
+            }
+        }
+    }
+    unsigned nbar = 0;
+    if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+    if (!kBatch && wib == 0) {
+        const double t = grid_total(a.partials, gridDim.x, lane, 1);
+        if (lane == 0) s_tpp = t;  // read after later CTA barriers
+    }
+    int sl_first = 0;  // the slice of this warp's first column
+    if constexpr (kBatch) {
+        if (crange.x < crange.y) sl_first = slice_index(a.sl_cols, a.ns, __ldg(a.nzc + crange.x));
+    }
+
+    // ---- jobs and their staging (warp-uniform) ----
+    // A job is J consecutive items of this warp's range: two rows (forward) or
+    // two column groups of GPW columns each (back). Lane k < J + 1 holds the
+    // job's pointer ptr[q + k] (clamped at the job's end), so every bound is
+    // one shuffle away. Jobs are pipelined three deep:
+    //   job j + 2: pointers and the first level of metadata (row or column index) load;
+    //   job j + 1: its bulk copy is issued and its remaining metadata loads;
+    //   job j:     waits for its copy and is processed.
+    auto load_ptrs = [&](const int32_t* ptr, int q, int qe) { return __ldg(ptr + min(q + lane, qe)); };
+    auto issue = [&](const int32_t* idx, const Pair* vals, int s, int lo, int hi) {
+        if (lane == 0) {
+            unsigned char* slot = wslots + (size_t)s * cap * kEB;
+            const unsigned nbi = 4u * (unsigned)(hi - lo), nbv = (unsigned)sizeof(Pair) * (unsigned)(hi - lo);
+            fence_proxy_async_smem();
+            mbar_expect_tx(&bar[s], nbi + nbv);
+            bulk_g2s(slot, idx + lo, nbi, &bar[s]);
+            bulk_g2s(slot + (size_t)cap * 4, vals + lo, nbv, &bar[s]);
+        }
+        inflight |= 1u << s;
+    };
+    // Wait (bounded) for every copy still in flight; used before leaving on an error.
+    auto drain = [&]() {
+        for (int s = 0; s < 2; ++s)
+            if (inflight & (1u << s)) mbar_wait_bounded(&bar[s], (phase >> s) & 1u, a.timeout_ns);
+        inflight = 0;
+    };
+    // Sums of two items' entries [loA, hiA) and [loB, hiB) (already offset), lane-strided by W.
+    // UC is std::integral_constant<int, gathers in flight per lane and item>.
+    auto two_items = [&](auto UC, const int32_t* idx, const Pair* vals, const V2* src, int loA, int hiA, int loB,
+                         int hiB, int first, int W, Acc& sA1, Acc& sA2, Acc& sB1, Acc& sB2) {
+        constexpr int U = decltype(UC)::value;
+        const int nA = hiA - loA, nB = hiB - loB, n = nA > nB ? nA : nB;
+        for (int base = first; base - first < n; base += U * W) {
+            V2 gA[U], gB[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int eA = loA + base + u * W, eB = loB + base + u * W;
+                if (eA < hiA) gA[u] = ldca(src + idx[eA]);
+                if (eB < hiB) gB[u] = ldca(src + idx[eB]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int eA = loA + base + u * W, eB = loB + base + u * W;
+                Acc v1, v2;
+                if (eA < hiA) {
+                    T::decode(vals[eA], v1, v2);
+                    sA1 += v1 * gA[u].x;
+                    sA2 += v2 * gA[u].y;
+                }
+                if (eB < hiB) {
+                    T::decode(vals[eB], v1, v2);
+                    sB1 += v1 * gB[u].x;
+                    sB2 += v2 * gB[u].y;
+                }
+            }
+        }
+    };
+    // One pass over the items [r0, r1). Meta is the per-item metadata one lane holds.
+    //   first(q, qe)        -> the first-level metadata load for job [q, qe) (returns an int);
+    //   second(q, qe, lvl1) -> the remaining metadata of the job (returns Meta);
+    //   body(q, qe, pv, soff, off, meta) processes the job. With soff >= 0 the job is
+    //   staged at byte soff of shared memory (entry e at position e - off); with
+    //   soff < 0 it is read from global memory.
+    // Returns false if a copy timed out.
+    auto run_pass = [&](const int32_t* ptr, const int32_t* idx, const Pair* vals, int r0, int r1, int J,
+                        auto&& first, auto&& second, auto&& body) {
+        if (r0 >= r1) return true;
+        int slot = 0;
+        // Job 0: pointers, copy and metadata, synchronously.
+        int q = r0, qe = min(q + J, r1);
+        int pv = load_ptrs(ptr, q, qe);
+        int lo = __shfl_sync(0xffffffffu, pv, 0) & ~3, hi = (__shfl_sync(0xffffffffu, pv, qe - q) + 3) & ~3;
+        bool st = hi - lo <= cap;
+        if (st) issue(idx, vals, slot, lo, hi);
+        auto meta = second(q, qe, first(q, qe));
+        // Job 1: pointers and first-level metadata.
+        int nq = qe, nqe = min(nq + J, r1);
+        int npv = nq < r1 ? load_ptrs(ptr, nq, nqe) : 0;
+        int nl1 = nq < r1 ? first(nq, nqe) : 0;
+        while (q < r1) {
+            // Job j + 1: copy and remaining metadata.
+            bool nst = false;
+            int nlo = 0;
+            decltype(meta) nmeta{};
+            if (nq < r1) {
+                nlo = __shfl_sync(0xffffffffu, npv, 0) & ~3;
+                const int nhi = (__shfl_sync(0xffffffffu, npv, nqe - nq) + 3) & ~3;
+                nst = nhi - nlo <= cap;
+                if (nst) issue(idx, vals, slot ^ 1, nlo, nhi);
+                nmeta = second(nq, nqe, nl1);
+            }
+            // Job j + 2: pointers and first-level metadata.
+            const int nnq = nqe, nnqe = min(nnq + J, r1);
+            const int nnpv = nnq < r1 ? load_ptrs(ptr, nnq, nnqe) : 0;
+            const int nnl1 = nnq < r1 ? first(nnq, nnqe) : 0;
+            // Job j.
+            if (st) {
+                if (!mbar_wait_bounded(&bar[slot], (phase >> slot) & 1u, a.timeout_ns)) {
+                    if (lane == 0 && atomicCAS(&a.ctl->err, 0, SPLITSART_ERR_TIMEOUT) == 0) a.ctl->err_where = -1;
+                    inflight &= ~(1u << slot);
+                    drain();
+                    return false;
+                }
+                phase ^= 1u << slot;
+                inflight &= ~(1u << slot);
+                body(q, qe, pv, (int)(wslots - smem_raw) + slot * cap * kEB, lo, meta);
+            } else {
+                body(q, qe, pv, -1, 0, meta);
+            }
+            __syncwarp();
+            q = nq;
+            qe = nqe;
+            pv = npv;
+            st = nst;
+            lo = nlo;
+            meta = nmeta;
+            nq = nnq;
+            nqe = nnqe;
+            npv = nnpv;
+            nl1 = nnl1;
+            slot ^= 1;
+        }
+        return true;
+    };
+
+    struct RowMeta {
+        int i;
+        V2 p;
+        N2 ir;
+        float2 sc;
+    };
+    struct ColMeta {
+        int j;  // -1: no column, or its slice has stopped
+        N2 ic;
+        V2 f;
+    };
+    constexpr int JB = 2 * GPW <= 31 ? 2 * GPW : 31;  // columns per back job (J + 1 pointers fit in a warp)
+
+    for (int k = 0;; ++k) {
+        // ---- forward: r = p - A f, u = r / R, and the norm partials ----
+        SqAcc<Acc> rr;  // lanes 0 and 1: their rows' ||r||^2
+        // Lane 0 holds row q's metadata, lane 1 row q + 1's.
+        auto f_first = [&](int q, int qe) { return (lane < 2 && q + lane < qe) ? __ldg(a.nzr + q + lane) : -1; };
+        auto f_second = [&](int, int, int i) {
+            RowMeta m{i, V2{}, N2{}, float2{}};
+            if (i >= 0) {
+                m.p = ldg(a.p12 + i);
+                m.ir = ldg(a.invR + i);
+                if constexpr (T::kQuant) m.sc = ldg(a.scale + i);
+            }
+            return m;
+        };
+        auto f_body = [&](int q, int qe, int pv, int soff, int off, const RowMeta& m) {
+            const int loA = __shfl_sync(0xffffffffu, pv, 0) - off, hiA = __shfl_sync(0xffffffffu, pv, 1) - off;
+            const int hiB = __shfl_sync(0xffffffffu, pv, qe - q) - off;  // = hiA when the job has one row
+            Acc sA1 = 0, sA2 = 0, sB1 = 0, sB2 = 0;
+            if (soff >= 0)
+                two_items(kUS, reinterpret_cast<const int32_t*>(smem_raw + soff),
+                          reinterpret_cast<const Pair*>(smem_raw + soff + cap * 4), a.f12, loA, hiA, hiA, hiB, lane, 32,
+                          sA1, sA2, sB1, sB2);
+            else
+                two_items(kUD, a.col, a.val, a.f12, loA, hiA, hiA, hiB, lane, 32, sA1, sA2, sB1, sB2);
+            sA1 = warp_sum(sA1);
+            sA2 = warp_sum(sA2);
+            sB1 = warp_sum(sB1);
+            sB2 = warp_sum(sB2);
+            if (m.i >= 0) {
+                Acc s1 = lane == 0 ? sA1 : sB1, s2 = lane == 0 ? sA2 : sB2;
+                if constexpr (T::kQuant) {
+                    s1 *= m.sc.x;
+                    s2 *= m.sc.y;
+                }
+                const Acc r1 = m.p.x - s1, r2 = m.p.y - s2;
+                // For BF16/FP16, ir already holds the row scale (the codes are reused by the back-projection).
+                stcg(a.u12 + m.i, V2{r1 * m.ir.x, r2 * m.ir.y});
+                if constexpr (kBatch) __stcg(a.rr_row + m.i, (double)(r1 * r1 + r2 * r2));
+                else rr.add(r1, r2);
+            }
+        };
+        const bool ok_f = run_pass(a.nzrp, a.col, a.val, rrange.x, rrange.y, 2, f_first, f_second, f_body);
+        if constexpr (!kBatch) {
+            const double t = warp_sum(rr.sum());
+            if (lane == 0) s_red[0][wib] = t;
+            __syncthreads();
+            if (wib == 0) {
+                const double tc = warp_sum(lane < nwarps ? s_red[0][lane] : 0.0);
+                if (lane == 0) __stcg(a.partials + 2 * blockIdx.x, tc + ppz);  // an empty row's residual is its p
+            }
+        }
+        (void)ok_f;  // a failed copy has recorded an error; the barrier below then returns false
+        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+
+        const bool last = (k >= a.max_iters);
+        if constexpr (kBatch) {
+            if (last || (k % a.check_every == 0)) {
+                for (int sl = gw; sl < a.ns; sl += nw_grid) {
+                    if (__ldcg(&a.sl_solve[sl].done)) continue;
+                    const double trr = warp_sum_range(a.rr_row, __ldg(a.sl_rows + sl), __ldg(a.sl_rows + sl + 1), lane);
+                    const double tpp = __ldcg(&a.sl_solve[sl].pp);
+                    const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
+                    if (lane == 0 && (last || rho <= a.tol)) {
+                        a.sl_solve[sl] = SliceSolve{k, 1, rho, trr, tpp};
+                        atomicAdd(a.ndone, 1);
+                    }
+                }
+            }
+            if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+            if (ld_volatile(a.ndone) >= a.ns) {
+                if (blockIdx.x == 0 && tid == 0) {
+                    a.result->iters = k;
+                    a.result->status = SPLITSART_OK;
+                    a.result->rho = 0.0;
+                    a.result->rr = 0.0;
+                    a.result->pp = 0.0;
+                }
+                return;
+            }
+        } else if (last || (k % a.check_every == 0)) {
+            if (wib == 0) {
+                const double t0 = grid_total(a.partials, gridDim.x, lane, 0);
+                if (lane == 0) s_red[0][0] = t0;
+            }
+            __syncthreads();
+            const double trr = s_red[0][0], tpp = s_tpp;
+            const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
+            if (last || rho <= a.tol) {
+                if (blockIdx.x == 0 && tid == 0) {
+                    a.result->iters = k;
+                    a.result->status = SPLITSART_OK;
+                    a.result->rho = rho;
+                    a.result->rr = trr;
+                    a.result->pp = tpp;
+                }
+                return;
+            }
+        }
+
+        // ---- back-projection and update: f += lambda (A^T u) / C ----
+        // Group g of LPC lanes takes columns q + g (A) and q + g + GPW (B). Its lane 0
+        // holds A's metadata, its lane 1 (lane 0 if LPC = 1) B's.
+        int sl = sl_first;  // this lane's slice, advanced as its columns increase
+        auto b_col = [&](int q, int qe) {
+            // With LPC = 1 every lane is a group's lane 0, and B is never in the job (J = 31).
+            const int g = lane / LPC;
+            int c = -1;
+            if (sub == 0) c = q + g;
+            else if (LPC > 1 && sub == 1) c = q + g + GPW;
+            return c < qe ? c : -1;
+        };
+        auto b_first = [&](int q, int qe) {
+            const int c = b_col(q, qe);
+            return c >= 0 ? __ldg(a.nzc + c) : -1;
+        };
+        auto b_second = [&](int, int, int j) {
+            ColMeta m{j, N2{}, V2{}};
+            if (j >= 0) {
+                if constexpr (kBatch) {
+                    while (j >= __ldg(a.sl_cols + sl + 1)) ++sl;
+                    if (__ldcg(&a.sl_solve[sl].done)) {  // the slice has stopped: keep its returned iterate
+                        m.j = -1;
+                        return m;
+                    }
+                }
+                m.ic = ldg(a.invC + j);
+                m.f = ldcg(a.f12 + j);
+            }
+            return m;
+        };
+        auto b_body = [&](int q, int qe, int pv, int soff, int off, const ColMeta& m) {
+            const int g = lane / LPC;
+            const int qA = q + g, qB = qA + GPW;
+            const int kA = min(g, 31), kB = min(g + GPW, 31);
+            const int pA0 = __shfl_sync(0xffffffffu, pv, kA), pA1 = __shfl_sync(0xffffffffu, pv, min(kA + 1, 31));
+            const int pB0 = __shfl_sync(0xffffffffu, pv, kB), pB1 = __shfl_sync(0xffffffffu, pv, min(kB + 1, 31));
+            const int loA = qA < qe ? pA0 - off : 0, hiA = qA < qe ? pA1 - off : 0;
+            const int loB = qB < qe ? pB0 - off : 0, hiB = qB < qe ? pB1 - off : 0;
+            Acc bA1 = 0, bA2 = 0, bB1 = 0, bB2 = 0;
+            if (soff >= 0)
+                two_items(kUS, reinterpret_cast<const int32_t*>(smem_raw + soff),
+                          reinterpret_cast<const Pair*>(smem_raw + soff + cap * 4), a.u12, loA, hiA, loB, hiB, sub, LPC,
+                          bA1, bA2, bB1, bB2);
+            else
+                two_items(kUD, a.row, a.valT, a.u12, loA, hiA, loB, hiB, sub, LPC, bA1, bA2, bB1, bB2);
+            bA1 = warp_sum(bA1, LPC);
+            bA2 = warp_sum(bA2, LPC);
+            bB1 = warp_sum(bB1, LPC);
+            bB2 = warp_sum(bB2, LPC);
+            if (m.j >= 0) {
+                const bool isA = LPC == 1 || sub == 0;
+                const Acc b1 = isA ? bA1 : bB1, b2 = isA ? bA2 : bB2;
+                V2 f = m.f;
+                f.x += lam * b1 * m.ic.x;
+                f.y += lam * b2 * m.ic.y;
+                stcg(a.f12 + m.j, f);
+            }
+        };
+        const bool ok_b = run_pass(a.nzcp, a.row, a.valT, crange.x, crange.y, JB, b_first, b_second, b_body);
+        (void)ok_b;
+        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+    }
+}
+
 template <class T>
 constexpr int default_tile_entries() {
     return sizeof(typename T::Vec2) == 16 ? 8192 : 12288;
@@ -900,22 +1618,43 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
         return fail(SPLITSART_ERR_ARG, "solve: the system does not fit in shared memory (need %lld of %lld bytes per SM)",
                     resident_bound<T>(fs, nsm), res_avail);
     const bool use_res = o.kernel == 2 || (o.kernel == 0 && res_ok);
+    const bool use_rows = o.kernel == 3 || (o.kernel == 0 && !res_ok);
+    const bool use_bulk = o.kernel == 4;
+    if (o.kernel < 0 || o.kernel > 4) return fail(SPLITSART_ERR_ARG, "solve: kernel must be 0, 1, 2, 3 or 4");
 
     SartArgs<T> a;
     void* kern;
     size_t dyn;
     int grid;
     int smem_bytes = 0;
+    int block = threads;
+    int te_bulk = 0;
     if (use_res) {
         kern = (void*)rkern;
         dyn = (size_t)res_avail;
         smem_bytes = (int)dyn;
         grid = nsm;
+        block = res_threads;
+    } else if (use_rows) {
+        kern = batch ? (void*)sart_rows_kernel<T, LPC, true> : (void*)sart_rows_kernel<T, LPC, false>;
+        dyn = 0;
+        block = threads > 512 ? 512 : threads;
+    } else if (use_bulk) {
+        kern = batch ? (void*)sart_bulk_kernel<T, LPC, true> : (void*)sart_bulk_kernel<T, LPC, false>;
+        block = threads > 384 ? 384 : threads;
+        cudaFuncAttributes ba{};
+        if ((e = cudaFuncGetAttributes(&ba, (const void*)kern)) != cudaSuccess) return cuda_fail(e, "solve: attributes");
+        // Two slots per warp, each a tile of te entries plus 8 of alignment slack.
+        const long long eb = 4 + (long long)sizeof(typename T::Pair);
+        const long long per_slot = ((long long)smem_optin - (long long)ba.sharedSizeBytes - 256) / (2LL * (block / 32) * eb);
+        te_bulk = (int)((per_slot - 8) & ~3LL);
+        if (te_bulk < 64) return fail(SPLITSART_ERR_ARG, "solve: too little shared memory for the bulk-staged kernel");
+        dyn = (size_t)(block / 32) * 2 * (size_t)(te_bulk + 8) * (size_t)eb;
     } else {
         kern = batch ? (void*)sart_stream_kernel<T, LPC, false, true> : (void*)sart_stream_kernel<T, LPC>;
         dyn = sizeof(typename T::Vec2) * (size_t)(o.tile_entries > 0 ? o.tile_entries : default_tile_entries<T>());
     }
-    if (!use_res) {
+    if (!use_res && !use_bulk) {
         cudaFuncAttributes sa{};
         if ((e = cudaFuncGetAttributes(&sa, (const void*)kern)) != cudaSuccess) return cuda_fail(e, "solve: attributes");
         if (dyn + sa.sharedSizeBytes > (size_t)smem_optin)
@@ -924,7 +1663,7 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
     e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return cuda_fail(e, "solve: shared memory attribute");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, use_res ? res_threads : threads, dyn);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, block, dyn);
     if (e != cudaSuccess) return cuda_fail(e, "solve: occupancy");
     if (per_sm < 1) return fail(SPLITSART_ERR_CUDA, "solve: kernel does not fit on an SM");
     if (!use_res) {
@@ -942,8 +1681,9 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
         return cuda_fail(e, "solve: memset");
     void* args_stream[] = {&a};
     void* args_res[] = {&a, &smem_bytes};
-    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(use_res ? res_threads : threads),
-                                    use_res ? args_res : args_stream, dyn, st);
+    void* args_bulk[] = {&a, &te_bulk};
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(block),
+                                    use_res ? args_res : (use_bulk ? args_bulk : args_stream), dyn, st);
     if (e != cudaSuccess) return cuda_fail(e, "solve: cooperative launch");
     return SPLITSART_OK;
 }

@@ -304,7 +304,7 @@ def test_resident_and_streaming_kernels_agree_with_oracle(ss, tiny, dt, tol):
     H2 = sp.csr_matrix((out["a2"], out["col"], out["row_ptr"]), shape=(Mh, Nh))
     ref = osart.split_sart(H1, H2, tiny.p1, tiny.p2, 1.0, 60)
     f_ref = osplit.recombine(ref["f1"], ref["f2"])
-    for kernel in (1, 2):
+    for kernel in (1, 2, 3, 4):
         info, f12, f = run_solve(ss, sysm, tiny.p, 60, 1.0, kernel=kernel)
         assert info["iters"] == 60
         assert rel(f, f_ref) <= tol, (kernel, rel(f, f_ref))
@@ -318,3 +318,6 @@ def test_realistic_kernels_agree(ss, realistic):
     a = run_solve(ss, sysm, c.p, 50, 0.8, kernel=1)
     b = run_solve(ss, sysm, c.p, 50, 0.8, kernel=2)
     assert rel(a[2], b[2]) <= 1e-5 and abs(a[0]["rho"] - b[0]["rho"]) <= 1e-5 * b[0]["rho"]
+    for kernel in (3, 4):
+        d = run_solve(ss, sysm, c.p, 50, 0.8, kernel=kernel)
+        assert rel(d[2], b[2]) <= 1e-5 and abs(d[0]["rho"] - b[0]["rho"]) <= 1e-5 * b[0]["rho"], kernel
