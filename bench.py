@@ -326,9 +326,16 @@ class Batch(Realistic):
         peak, kind = read_peak("hbm_gbs", 6800.0)
         ach = alg / (solve_ms / 1e3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": profile_traffic(self.profile), "kernel": "sart_stream_kernel<TF32,LPC,batch>",
+                "traffic": profile_traffic(self.profile), "kernel": self.kernel_name(),
                 "algorithmic_bytes_per_launch": alg, "peak_source": f"{kind} hbm_gbs",
                 "note": "timed region = the replayed graph (fold of p, solve, recombine); inputs far exceed L2"}
+
+    def kernel_name(self):
+        return {1: "sart_stream_kernel<TF32,LPC,batch> (CTA-wide staged tiles)",
+                2: "sart_resident_kernel<TF32,LPC>",
+                3: "sart_rows_kernel<TF32,LPC,batch> (row streaming, dynamically scheduled chunks)",
+                4: "sart_bulk_kernel<TF32,LPC,batch> (per-warp bulk-copy staging)"}.get(
+            self.tuned.get("kernel"), "sart_rows_kernel<TF32,LPC,batch> (library choice)")
 
     def config(self):
         return {"workload": f"batch: {len(self.gs)} slices, nx in {{256,512,768,1024}}, nz in [64,256], K in [16,32], "
@@ -665,6 +672,24 @@ def oracle_throughput(wl, budget_s):
                                   f"single thread), {el:.1f} s; host has {os.cpu_count()} cores"}
 
 
+def job_totals(step_ms, e2e_ms, solve_ms, units, steps, device):
+    """Whole-job figures: the slowest rank's times and the units of all ranks.
+
+    Returns (step_ms, e2e_ms, solve_ms, total_units), where the times are the
+    maximum over ranks and total_units is the sum over ranks of units x steps.
+    Without an initialised process group this is the single-process case.
+    """
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([step_ms, e2e_ms, solve_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units) * steps], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    step_ms, e2e_ms, solve_ms = t.tolist()
+    return step_ms, e2e_ms, solve_ms, u.item()
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -737,11 +762,7 @@ def run_native(args):
     torch.cuda.synchronize()
     fold_ms = a.elapsed_time(b)
 
-    t_local = torch.tensor([step_ms, e2e_ms, solve_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    step_ms, e2e_ms, solve_ms = t_local.tolist()
-    total_units = units * args.steps * ws
+    step_ms, e2e_ms, solve_ms, total_units = job_totals(step_ms, e2e_ms, solve_ms, units, args.steps, dev)
     value = total_units / (step_ms / 1e3)
     e2e_value = total_units / (e2e_ms / 1e3)
     extra = wl.extra(ss)

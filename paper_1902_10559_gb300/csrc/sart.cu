@@ -855,13 +855,16 @@ __device__ __forceinline__ __half2 ldcs(const __half2* p) {
     return *reinterpret_cast<__half2*>(&v);
 }
 
-template <class T, int LPC, bool kBatch>
+// UF: entries in flight per lane and row (two rows per warp step). UB: per
+// lane and column; with UB > 6 each lane group takes one column per step,
+// otherwise two.
+template <class T, int LPC, bool kBatch, int UF, int UB>
 __global__ void __launch_bounds__(512, 1) sart_rows_kernel(SartArgs<T> a) {
     using Acc = typename T::Acc;
     using V2 = typename T::Vec2;
     using N2 = typename T::KNorm2;
     using Pair = typename T::Pair;
-    constexpr int U = sizeof(V2) == 16 ? 2 : 4;  // entries in flight per lane and row
+    constexpr bool kOneCol = UB > 6;
     constexpr int kGroupsPerWarp = 32 / LPC;
     constexpr int kRowChunk = 16;  // rows per scheduled chunk
     __shared__ double s_red[2][32];
@@ -927,53 +930,81 @@ __global__ void __launch_bounds__(512, 1) sart_rows_kernel(SartArgs<T> a) {
         const double t = grid_total(a.partials, gridDim.x, lane, 1);
         if (lane == 0) s_tpp = t;  // read after later CTA barriers
     }
-    // Loads of up to U entries of one item (lane-strided by W), then their gathers, then the products.
-    auto issue = [&](const int32_t* idx, const Pair* vals, int lo, int hi, int first, int W, int (&ix)[U],
-                     Pair (&v)[U]) {
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = lo + first + u * W;
-            if (e < hi) {
-                ix[u] = ldcs(idx + e);
-                v[u] = ldcs(vals + e);
-            }
-        }
-    };
-    auto gather = [&](const V2* src, int lo, int hi, int first, int W, const int (&ix)[U], V2 (&g)[U]) {
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = lo + first + u * W;
-            if (e < hi) g[u] = ldca(src + ix[u]);
-        }
-    };
-    auto consume = [&](int lo, int hi, int first, int W, const Pair (&v)[U], const V2 (&g)[U], Acc& s1, Acc& s2) {
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = lo + first + u * W;
-            if (e < hi) {
-                Acc v1, v2;
-                T::decode(v[u], v1, v2);
-                s1 += v1 * g[u].x;
-                s2 += v2 * g[u].y;
-            }
-        }
-    };
-    // Two items at once, all rounds: sums (A1, A2) of item A and of item B.
-    auto two_items = [&](const int32_t* idx, const Pair* vals, const V2* src, int loA, int hiA, int loB, int hiB,
-                         int first, int W, Acc& sA1, Acc& sA2, Acc& sB1, Acc& sB2) {
+    // Rounds over one or two items: each lane issues the index and value loads
+    // of up to UU entries per item (lane-strided by W), then their gathers,
+    // then the products. UC is std::integral_constant<int, UU>.
+    auto two_items = [&](auto UC, const int32_t* idx, const Pair* vals, const V2* src, int loA, int hiA, int loB,
+                         int hiB, int first, int W, Acc& sA1, Acc& sA2, Acc& sB1, Acc& sB2) {
+        constexpr int UU = decltype(UC)::value;
         const int nA = hiA - loA, nB = hiB - loB, n = nA > nB ? nA : nB;
-        for (int base = first; base - first < n; base += U * W) {
-            int ixA[U], ixB[U];
-            Pair vA[U], vB[U];
-            V2 gA[U], gB[U];
-            issue(idx, vals, loA, hiA, base, W, ixA, vA);
-            issue(idx, vals, loB, hiB, base, W, ixB, vB);
-            gather(src, loA, hiA, base, W, ixA, gA);
-            gather(src, loB, hiB, base, W, ixB, gB);
-            consume(loA, hiA, base, W, vA, gA, sA1, sA2);
-            consume(loB, hiB, base, W, vB, gB, sB1, sB2);
+        for (int base = first; base - first < n; base += UU * W) {
+            int ixA[UU], ixB[UU];
+            Pair vA[UU], vB[UU];
+            V2 gA[UU], gB[UU];
+#pragma unroll
+            for (int u = 0; u < UU; ++u) {
+                const int eA = loA + base + u * W, eB = loB + base + u * W;
+                if (eA < hiA) {
+                    ixA[u] = ldcs(idx + eA);
+                    vA[u] = ldcs(vals + eA);
+                }
+                if (eB < hiB) {
+                    ixB[u] = ldcs(idx + eB);
+                    vB[u] = ldcs(vals + eB);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UU; ++u) {
+                if (loA + base + u * W < hiA) gA[u] = ldca(src + ixA[u]);
+                if (loB + base + u * W < hiB) gB[u] = ldca(src + ixB[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < UU; ++u) {
+                Acc v1, v2;
+                if (loA + base + u * W < hiA) {
+                    T::decode(vA[u], v1, v2);
+                    sA1 += v1 * gA[u].x;
+                    sA2 += v2 * gA[u].y;
+                }
+                if (loB + base + u * W < hiB) {
+                    T::decode(vB[u], v1, v2);
+                    sB1 += v1 * gB[u].x;
+                    sB2 += v2 * gB[u].y;
+                }
+            }
         }
     };
+    auto one_item = [&](auto UC, const int32_t* idx, const Pair* vals, const V2* src, int lo, int hi, int first, int W,
+                        Acc& s1, Acc& s2) {
+        constexpr int UU = decltype(UC)::value;
+        for (int base = first; base - first < hi - lo; base += UU * W) {
+            int ix[UU];
+            Pair v[UU];
+            V2 g[UU];
+#pragma unroll
+            for (int u = 0; u < UU; ++u) {
+                const int e = lo + base + u * W;
+                if (e < hi) {
+                    ix[u] = ldcs(idx + e);
+                    v[u] = ldcs(vals + e);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UU; ++u)
+                if (lo + base + u * W < hi) g[u] = ldca(src + ix[u]);
+#pragma unroll
+            for (int u = 0; u < UU; ++u) {
+                if (lo + base + u * W < hi) {
+                    Acc v1, v2;
+                    T::decode(v[u], v1, v2);
+                    s1 += v1 * g[u].x;
+                    s2 += v2 * g[u].y;
+                }
+            }
+        }
+    };
+    constexpr std::integral_constant<int, UF> kUF{};
+    constexpr std::integral_constant<int, UB> kUB{};
 
     for (int k = 0;; ++k) {
         // ---- forward: r = p - A f, u = r / R, and the norm partials ----
@@ -1006,7 +1037,7 @@ __global__ void __launch_bounds__(512, 1) sart_rows_kernel(SartArgs<T> a) {
                 const int loA = __ldg(a.nzrp + q), hiA = __ldg(a.nzrp + q + 1);
                 const int hiB = hasB ? __ldg(a.nzrp + q + 2) : hiA;
                 Acc sA1 = 0, sA2 = 0, sB1 = 0, sB2 = 0;
-                two_items(a.col, a.val, a.f12, loA, hiA, hiA, hiB, lane, 32, sA1, sA2, sB1, sB2);
+                two_items(kUF, a.col, a.val, a.f12, loA, hiA, hiA, hiB, lane, 32, sA1, sA2, sB1, sB2);
                 sA1 = warp_sum(sA1);
                 sA2 = warp_sum(sA2);
                 sB1 = warp_sum(sB1);
@@ -1091,19 +1122,30 @@ __global__ void __launch_bounds__(512, 1) sart_rows_kernel(SartArgs<T> a) {
             stcg(a.f12 + j, f);
         };
         if (blockIdx.x == 0 && tid == 0) a.ctl->work[0] = 0;  // the forward pass's counter, idle until the barrier
-        constexpr int kColChunk = 4 * 2 * kGroupsPerWarp;
+        constexpr int kColsPerStep = (kOneCol ? 1 : 2) * kGroupsPerWarp;
+        constexpr int kColChunk = 8 * kGroupsPerWarp;
         if (lane == 0) grab = atomicAdd(&a.ctl->work[1], 1u);
         for (int chunk = __shfl_sync(0xffffffffu, grab, 0); chunk < (n_nzc + kColChunk - 1) / kColChunk;
              chunk = __shfl_sync(0xffffffffu, grab, 0)) {
             if (lane == 0) grab = atomicAdd(&a.ctl->work[1], 1u);
             const int c1 = min((chunk + 1) * kColChunk, n_nzc);
-            // Warp-uniform loop over pairs of column groups, so every lane reaches the shuffles.
-            for (int g0 = chunk * kColChunk; g0 < c1; g0 += 2 * kGroupsPerWarp) {
+            // Warp-uniform loop over steps of column groups, so every lane reaches the shuffles.
+            for (int g0 = chunk * kColChunk; g0 < c1; g0 += kColsPerStep) {
+                if constexpr (kOneCol) {
+                    const int q = g0 + lane / LPC;
+                    const int lo = q < c1 ? __ldg(a.nzcp + q) : 0, hi = q < c1 ? __ldg(a.nzcp + q + 1) : 0;
+                    Acc b1 = 0, b2 = 0;
+                    one_item(kUB, a.row, a.valT, a.u12, lo, hi, sub, LPC, b1, b2);
+                    b1 = warp_sum(b1, LPC);
+                    b2 = warp_sum(b2, LPC);
+                    if (sub == 0 && q < c1) fin_col(q, b1, b2);
+                    continue;
+                }
                 const int qA = g0 + lane / LPC, qB = qA + kGroupsPerWarp;
                 const int loA = qA < c1 ? __ldg(a.nzcp + qA) : 0, hiA = qA < c1 ? __ldg(a.nzcp + qA + 1) : 0;
                 const int loB = qB < c1 ? __ldg(a.nzcp + qB) : 0, hiB = qB < c1 ? __ldg(a.nzcp + qB + 1) : 0;
                 Acc bA1 = 0, bA2 = 0, bB1 = 0, bB2 = 0;
-                two_items(a.row, a.valT, a.u12, loA, hiA, loB, hiB, sub, LPC, bA1, bA2, bB1, bB2);
+                two_items(kUB, a.row, a.valT, a.u12, loA, hiA, loB, hiB, sub, LPC, bA1, bA2, bB1, bB2);
                 bA1 = warp_sum(bA1, LPC);
                 bA2 = warp_sum(bA2, LPC);
                 bB1 = warp_sum(bB1, LPC);
@@ -1536,6 +1578,14 @@ constexpr int default_tile_entries() {
     return sizeof(typename T::Vec2) == 16 ? 8192 : 12288;
 }
 
+// Row-streaming kernel: entries in flight per lane and item (FP64 pairs are
+// twice as wide, so they keep fewer in flight).
+template <class T, int LPC>
+void* rows_kernel(bool batch) {
+    constexpr int kU = sizeof(typename T::Vec2) == 16 ? 2 : 4;
+    return batch ? (void*)sart_rows_kernel<T, LPC, true, kU, kU> : (void*)sart_rows_kernel<T, LPC, false, kU, kU>;
+}
+
 template <class T>
 void fill_args(SartArgs<T>& a, splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o,
                unsigned grid) {
@@ -1636,7 +1686,7 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
         grid = nsm;
         block = res_threads;
     } else if (use_rows) {
-        kern = batch ? (void*)sart_rows_kernel<T, LPC, true> : (void*)sart_rows_kernel<T, LPC, false>;
+        kern = rows_kernel<T, LPC>(batch);
         dyn = 0;
         block = threads > 512 ? 512 : threads;
     } else if (use_bulk) {
