@@ -266,7 +266,7 @@ class Realistic:
 class Batch(Realistic):
     name = "batch"
     config_id = 3
-    profile = "sart_stream_batch_fp32.txt"
+    profile = "sart_rows_batch256_fp32.txt"
     n_slices = 256
 
     def setup(self, ss, dev, rank):

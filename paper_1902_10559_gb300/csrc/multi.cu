@@ -6,15 +6,21 @@
 // stopping test; only the matrix is shared.
 //
 // Layout. The whole folded system (CSR, CSC, normalisers) is copied into each
-// CTA's shared memory once per launch. Each CTA owns RC right-hand sides, with
-// their p, u and f also in shared memory. An iteration therefore touches no
-// global memory, and the two phases are separated by CTA barriers only. The
-// launch needs no grid-wide synchronisation.
+// CTA's shared memory once per launch. Each CTA has RC slots, each holding one
+// right-hand side's p, u and f, also in shared memory. An iteration therefore
+// touches no global memory, and the two phases are separated by CTA barriers
+// only. The launch needs no grid-wide synchronisation.
 //
-// SpMM. A warp takes one row (forward) or one column (back). Its 32 lanes are
-// split into RC groups of 32/RC lanes, one group per right-hand side. Every
-// matrix entry read from shared memory (a broadcast) is applied to all RC
-// right-hand sides.
+// Scheduling. The launch is persistent: as many CTAs as are resident at once.
+// When a slot's right-hand side stops, its f and stop record are written out
+// and the slot takes the next right-hand side from a global queue. The launch
+// time then follows the total iterations of all right-hand sides, not the
+// slowest one per CTA. Each right-hand side is computed within one slot in a
+// fixed order, so results do not depend on the schedule.
+//
+// SpMM. A warp takes RPW rows (forward) or columns (back) at a time. Its 32
+// lanes are split into RPW x RC groups, one per (row, slot). Every matrix
+// entry read from shared memory (a broadcast) is applied to all RC slots.
 #include <cmath>
 #include <cstdio>
 
@@ -39,6 +45,7 @@ struct MultiArgs {
     const typename T::Vec2* p12;  // [nrhs][Mh]
     typename T::Vec2* f12;        // [nrhs][Nh]
     splitsart_solve_info* info;   // [nrhs]
+    unsigned* queue;              // next right-hand side after the first wave (zeroed before the launch)
     int Mh, Nh, S, nrhs;
     int max_iters, check_every;
     double lambda, tol;
@@ -59,12 +66,15 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_rr[16][RPW][RC];
     __shared__ double s_pp[RC];
-    __shared__ int s_done[RC], s_ndone;
+    __shared__ int s_rhs[RC];    // right-hand side held by each slot, or -1
+    __shared__ int s_k[RC];      // iterations done by the slot's right-hand side
+    __shared__ int s_fresh[RC];  // refilled in this pass: no update until its first forward pass
+    __shared__ unsigned s_fin;   // slots whose right-hand side stopped in this pass
+    __shared__ int s_active;
 
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nwarps = blockDim.x >> 5;
     const int grp = lane / LPR, sub = lane % LPR;
-    const int g = grp % RC, rw = grp / RC;        // right-hand side and row slot of this lane group
-    const int r0 = blockIdx.x * RC;                // first right-hand side of this CTA
+    const int g = grp % RC, rw = grp / RC;        // slot and row of this lane group
     const int Mh = a.Mh, Nh = a.Nh, S = a.S;
     const Acc lam = (Acc)a.lambda;
 
@@ -106,34 +116,49 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
         if constexpr (T::kQuant) s_sc[i] = a.scale[i];
     }
     for (int j = tid; j < Nh; j += blockDim.x) s_ic[j] = a.invC[j];
-    for (int t = tid; t < Mh * RC; t += blockDim.x) {
-        const int i = t / RC, r = t % RC;
-        s_p[t] = r0 + r < a.nrhs ? a.p12[(size_t)(r0 + r) * Mh + i] : V2{};
-    }
-    for (int t = tid; t < Nh * RC; t += blockDim.x) {
-        const int j = t / RC, r = t % RC;
-        s_f[t] = r0 + r < a.nrhs ? a.f12[(size_t)(r0 + r) * Nh + j] : V2{};
+    // ---- slots: load, store, and ||p||^2 of newly loaded right-hand sides ----
+    auto load_slots = [&](unsigned mask) {
+        for (int t = tid; t < Mh * RC; t += blockDim.x) {
+            const int i = t / RC, r = t % RC;
+            if (mask >> r & 1u) s_p[t] = s_rhs[r] >= 0 ? a.p12[(size_t)s_rhs[r] * Mh + i] : V2{};
+        }
+        for (int t = tid; t < Nh * RC; t += blockDim.x) {
+            const int j = t / RC, r = t % RC;
+            if (mask >> r & 1u) s_f[t] = s_rhs[r] >= 0 ? a.f12[(size_t)s_rhs[r] * Nh + j] : V2{};
+        }
+        __syncthreads();
+        // ||p||^2 once per right-hand side: one warp per slot, lane-strided, fixed tree.
+        for (int r = wib; r < RC; r += nwarps) {
+            if (!(mask >> r & 1u)) continue;
+            double t1 = 0.0;
+            for (int i = lane; i < Mh; i += 32) {
+                const V2 p = s_p[i * RC + r];
+                t1 += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+            }
+            t1 = warp_sum(t1);
+            if (lane == 0) s_pp[r] = t1;
+        }
+    };
+    auto store_slots = [&](unsigned mask) {
+        for (int t = tid; t < Nh * RC; t += blockDim.x) {
+            const int j = t / RC, r = t % RC;
+            if ((mask >> r & 1u) && s_rhs[r] >= 0) a.f12[(size_t)s_rhs[r] * Nh + j] = s_f[t];
+        }
+    };
+
+    // The first wave of right-hand sides is blockIdx.x * RC + r; later ones come from the queue.
+    if (tid < RC) {
+        const int r = blockIdx.x * RC + tid;
+        s_rhs[tid] = r < a.nrhs ? r : -1;
+        s_k[tid] = 0;
+        s_fresh[tid] = 0;
     }
     __syncthreads();
-    if (tid < RC) {
-        // ||p||^2 of each right-hand side, once, in a fixed order.
-        double t1 = 0.0;
-        for (int i = 0; i < Mh; ++i) {
-            const V2 p = s_p[i * RC + tid];
-            t1 += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
-        }
-        s_pp[tid] = t1;
-        s_done[tid] = (r0 + tid >= a.nrhs);  // padding right-hand sides count as done
-    }
-    if (tid == 0) {
-        int n = 0;
-        for (int r = 0; r < RC; ++r) n += (r0 + r >= a.nrhs);
-        s_ndone = n;
-    }
+    load_slots((1u << RC) - 1u);
     __syncthreads();
 
-    for (int k = 0;; ++k) {
-        // ---- forward: RPW rows per warp, one lane group per (row, right-hand side) ----
+    for (;;) {
+        // ---- forward: RPW rows per warp, one lane group per (row, slot) ----
         SqAcc<Acc> rr;  // this lane group's ||r||^2 over its rows
         for (int i0 = wib * RPW; i0 < Mh; i0 += nwarps * RPW) {
             const int i = i0 + rw;
@@ -165,26 +190,49 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
             }
         }
         if (sub == 0) s_rr[wib][rw][g] = rr.sum();
+        if (tid == 0) s_fin = 0u;
         __syncthreads();
-        // ---- stop tests, one thread per right-hand side, fixed order ----
-        const bool last = k >= a.max_iters;
-        if (last || (k % a.check_every == 0)) {
-            if (tid < RC && !s_done[tid]) {
+        // ---- stop tests, one thread per slot, fixed order ----
+        if (tid < RC && s_rhs[tid] >= 0) {
+            const int k = s_k[tid];
+            const bool last = k >= a.max_iters;
+            if (last || (k % a.check_every == 0)) {
                 double t0 = 0.0;
                 for (int w = 0; w < nwarps; ++w)
                     for (int q = 0; q < RPW; ++q) t0 += s_rr[w][q][tid];
                 const double t1 = s_pp[tid];
                 const double rho = t1 > 0.0 ? sqrt(t0 / t1) : 0.0;
                 if (last || rho <= a.tol) {
-                    s_done[tid] = 1;
-                    a.info[r0 + tid] = splitsart_solve_info{k, SPLITSART_OK, rho, t0, t1};
-                    atomicAdd(&s_ndone, 1);
+                    a.info[s_rhs[tid]] = splitsart_solve_info{k, SPLITSART_OK, rho, t0, t1};
+                    atomicOr(&s_fin, 1u << tid);
                 }
             }
-            __syncthreads();
-            if (s_ndone >= RC) break;
         }
-        // ---- back-projection and update for the right-hand sides still running ----
+        __syncthreads();
+        const unsigned fin = s_fin;
+        if (fin) {
+            // Return the stopped right-hand sides' f and refill their slots from the queue.
+            store_slots(fin);
+            __syncthreads();
+            if (tid == 0) {
+                int active = 0;
+                for (int r = 0; r < RC; ++r) {
+                    if (fin >> r & 1u) {
+                        const int nxt = (int)atomicAdd(a.queue, 1u) + (int)gridDim.x * RC;
+                        s_rhs[r] = nxt < a.nrhs ? nxt : -1;
+                        s_k[r] = 0;
+                        s_fresh[r] = 1;
+                    }
+                    active += s_rhs[r] >= 0;
+                }
+                s_active = active;
+            }
+            __syncthreads();
+            if (s_active == 0) break;
+            load_slots(fin);
+            __syncthreads();
+        }
+        // ---- back-projection and update for the slots still running ----
         for (int j0 = wib * RPW; j0 < Nh; j0 += nwarps * RPW) {
             const int j = j0 + rw;
             Acc b1 = 0, b2 = 0;
@@ -200,7 +248,7 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
             }
             b1 = warp_sum(b1, LPR);
             b2 = warp_sum(b2, LPR);
-            if (sub == 0 && j < Nh && !s_done[g]) {
+            if (sub == 0 && j < Nh && s_rhs[g] >= 0 && !s_fresh[g]) {
                 const N2 ic = s_ic[j];
                 V2 f = s_f[j * RC + g];
                 f.x += lam * b1 * ic.x;
@@ -209,10 +257,11 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
             }
         }
         __syncthreads();
-    }
-    for (int t = tid; t < Nh * RC; t += blockDim.x) {
-        const int j = t / RC, r = t % RC;
-        if (r0 + r < a.nrhs) a.f12[(size_t)(r0 + r) * Nh + j] = s_f[t];
+        if (tid < RC) {
+            if (s_rhs[tid] >= 0 && !s_fresh[tid]) ++s_k[tid];
+            s_fresh[tid] = 0;
+        }
+        __syncthreads();
     }
 }
 
@@ -270,7 +319,18 @@ int launch_multi(splitsart_system* s, int S, int nrhs, const void* p12, void* f1
     const int threads = o.block_threads > 0 ? o.block_threads : 512;
     if (threads % 32 || threads > 512 || threads < 32)
         return fail(SPLITSART_ERR_ARG, "solve_multi: block_threads must be a multiple of 32 in [32, 512]");
-    const int grid = (nrhs + RC - 1) / RC;
+    // Persistent: as many CTAs as are resident at once; a CTA refills a slot from
+    // the queue as soon as its right-hand side stops.
+    int nsm = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, threads, dyn);
+    if (e != cudaSuccess) return cuda_fail(e, "solve_multi: occupancy");
+    if (per_sm < 1) return fail(SPLITSART_ERR_ARG, "solve_multi: the kernel does not fit on an SM");
+    const int groups = (nrhs + RC - 1) / RC;
+    const int grid = groups < nsm * per_sm ? groups : nsm * per_sm;
+    a.queue = &s->ctl->work[0];
+    if ((e = cudaMemsetAsync(s->ctl, 0, sizeof(LaunchCtl), st)) != cudaSuccess)
+        return cuda_fail(e, "solve_multi: memset");
     kern<<<grid, threads, dyn, st>>>(a);
     e = cudaGetLastError();
     return e == cudaSuccess ? SPLITSART_OK : cuda_fail(e, "solve_multi: launch");
