@@ -13,6 +13,10 @@
 // - A deterministic CSC transpose. Columns are counted, scanned and placed
 //   with atomics, then each column is sorted by row. The absolute row and
 //   column sums come last, in FP64, with 1/0 := 0.
+// The per-row and per-column kernels run one warp per item. A half row is
+// staged in shared memory with coalesced loads, and the union of its two
+// sorted lists is formed by a merge path whose positions are split evenly
+// over the lanes, so the FP64 work is spread over all 32 lanes.
 #include <climits>
 #include <cstdio>
 
@@ -27,35 +31,63 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-// Visit folded row i in ascending column order. Call fn(col, w_direct, w_reflected),
-// with 0.0 for an absent side.
-template <class F>
-__device__ __forceinline__ void for_each_folded(const int32_t* __restrict__ hcol, const double* __restrict__ hval,
-                                                int64_t e0, int64_t e1, int N, F&& fn) {
-    const int Nh = N >> 1;
-    int64_t lo = e0, hi = e1;
+// Warp-per-item kernels: warps per block, and the entries one warp stages in
+// shared memory (longer items are read from global memory instead).
+constexpr int kFoldWarps = 8;
+constexpr int kRowCap = 1024;  // half-row entries
+constexpr int kColCap = 256;   // CSC column entries
+
+// The two ascending lists of half row i: L, its entries with column < N/2 in
+// stored order, and R', its entries with column >= N/2 read backward and
+// reflected to N-1-j. c and v point at the row's stored columns and values
+// (in shared or in global memory); nL is the length of L.
+struct HalfRow {
+    const int32_t* c;
+    const double* v;
+    int n, nL, N;
+    __device__ __forceinline__ int Lc(int a) const { return c[a]; }
+    __device__ __forceinline__ int Rc(int b) const { return N - 1 - c[n - 1 - b]; }
+    __device__ __forceinline__ double Lv(int a) const { return v[a]; }
+    __device__ __forceinline__ double Rv(int b) const { return v[n - 1 - b]; }
+};
+
+// Merge path: the number of L items among the first d items of the merged
+// order, in which L goes first on equal columns.
+__device__ __forceinline__ int merge_split(const HalfRow& h, int d) {
+    int lo = max(0, d - (h.n - h.nL)), hi = min(d, h.nL);
     while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (hcol[mid] < Nh) lo = mid + 1;
+        const int mid = (lo + hi) >> 1;
+        if (h.Lc(mid) <= h.Rc(d - mid - 1)) lo = mid + 1;
         else hi = mid;
     }
-    const int64_t m = lo;
-    int64_t a = e0, b = e1 - 1;
-    while (a < m || b >= m) {
-        const int ca = a < m ? hcol[a] : INT_MAX;
-        const int cb = b >= m ? (N - 1 - hcol[b]) : INT_MAX;
-        if (ca < cb) {
-            fn(ca, hval[a], 0.0);
+    return lo;
+}
+
+// Visit the merged positions [d0, d1) in ascending column order and call
+// fn(col, w_direct, w_reflected) once per folded column, with 0.0 for an
+// absent side. A column in both lists is visited at its L item; its R' twin,
+// which comes next in the merged order, is skipped wherever it falls.
+template <class F>
+__device__ __forceinline__ void merge_walk(const HalfRow& h, int d0, int d1, F&& fn) {
+    const int nR = h.n - h.nL;
+    int a = merge_split(h, d0), b = d0 - a;
+    for (int d = d0; d < d1; ++d) {
+        if (a < h.nL && (b >= nR || h.Lc(a) <= h.Rc(b))) {
+            const int c = h.Lc(a);
+            const bool twin = b < nR && h.Rc(b) == c;
+            fn(c, h.Lv(a), twin ? h.Rv(b) : 0.0);
             ++a;
-        } else if (cb < ca) {
-            fn(cb, 0.0, hval[b]);
-            --b;
         } else {
-            fn(ca, hval[a], hval[b]);
-            ++a;
-            --b;
+            const int c = h.Rc(b);
+            if (!(a > 0 && h.Lc(a - 1) == c)) fn(c, 0.0, h.Rv(b));
+            ++b;
         }
     }
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
 // The slice holding global index i: the largest s with off[s] <= i.
@@ -69,16 +101,50 @@ __device__ __forceinline__ int slice_of(const long long* off, int ns, long long 
     return lo;
 }
 
-__global__ void fold_count_kernel(int64_t Mh, SliceMap sm, const int64_t* __restrict__ hrp,
-                                  const int32_t* __restrict__ hcol, const double* __restrict__ hval,
-                                  int32_t* __restrict__ cnt) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// One warp stages half row i (warp-uniform): returns the HalfRow view.
+__device__ __forceinline__ HalfRow stage_half_row(const int64_t* __restrict__ hrp, const int32_t* __restrict__ hcol,
+                                                  const double* __restrict__ hval, int64_t i, int N, int32_t* sc,
+                                                  double* sv, int lane) {
+    const int64_t e0 = hrp[i];
+    const int n = (int)(hrp[i + 1] - e0);
+    const bool staged = n <= kRowCap;
+    const int Nh = N >> 1;
+    int nL = 0;
+    for (int t0 = 0; t0 < n; t0 += 32) {
+        const int t = t0 + lane;
+        int c = INT_MAX;
+        if (t < n) {
+            c = hcol[e0 + t];
+            if (staged) {
+                sc[t] = c;
+                sv[t] = hval[e0 + t];
+            }
+        }
+        nL += __popc(__ballot_sync(0xffffffffu, c < Nh));
+    }
+    __syncwarp();
+    return staged ? HalfRow{sc, sv, n, nL, N} : HalfRow{hcol + e0, hval + e0, n, nL, N};
+}
+
+// Folded entries per row: one warp per row, the merged order split evenly over the lanes.
+__global__ void __launch_bounds__(kFoldWarps * 32) fold_count_kernel(int64_t Mh, SliceMap sm,
+                                                                     const int64_t* __restrict__ hrp,
+                                                                     const int32_t* __restrict__ hcol,
+                                                                     const double* __restrict__ hval,
+                                                                     int32_t* __restrict__ cnt) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = blockIdx.x * (int64_t)kFoldWarps + w;
     if (i >= Mh) return;
+    double* sv = reinterpret_cast<double*>(smem) + (size_t)w * kRowCap;
+    int32_t* sc = reinterpret_cast<int32_t*>(smem + (size_t)kFoldWarps * kRowCap * 8) + (size_t)w * kRowCap;
     const int s = slice_of(sm.rows, sm.ns, i);
-    const int N = (int)(sm.N[s + 1] - sm.N[s]);
+    const HalfRow h = stage_half_row(hrp, hcol, hval, i, (int)(sm.N[s + 1] - sm.N[s]), sc, sv, lane);
     int n = 0;
-    for_each_folded(hcol, hval, hrp[i], hrp[i + 1], N, [&](int, double, double) { ++n; });
-    cnt[i] = n;
+    merge_walk(h, (int)((long long)lane * h.n / 32), (int)((long long)(lane + 1) * h.n / 32),
+               [&](int, double, double) { ++n; });
+    n = warp_sum(n);
+    if (lane == 0) cnt[i] = n;
 }
 
 // Exclusive scan of cnt[0..n) into out[0..n]; out[n] = total.
@@ -198,54 +264,74 @@ __device__ __forceinline__ void store_pair(typename T::Pair* p, double a1, doubl
     }
 }
 
+// Folded row i: columns, value pairs (quantised with the row's scales for
+// BF16/FP16), and the FP64 absolute row sums of the stored values.
 template <class T>
-__global__ void fold_fill_kernel(int64_t Mh, SliceMap sm, const int64_t* __restrict__ hrp,
-                                 const int32_t* __restrict__ hcol, const double* __restrict__ hval,
-                                 const int32_t* __restrict__ frp, int32_t* __restrict__ col,
-                                 typename T::Pair* __restrict__ val, double2* __restrict__ Rsum,
-                                 typename T::Norm2* __restrict__ invR, float2* __restrict__ scale,
-                                 float2* __restrict__ wR, FoldStats* __restrict__ stats) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kFoldWarps * 32) fold_fill_kernel(
+    int64_t Mh, SliceMap sm, const int64_t* __restrict__ hrp, const int32_t* __restrict__ hcol,
+    const double* __restrict__ hval, const int32_t* __restrict__ frp, int32_t* __restrict__ col,
+    typename T::Pair* __restrict__ val, double2* __restrict__ Rsum, typename T::Norm2* __restrict__ invR,
+    float2* __restrict__ scale, float2* __restrict__ wR, FoldStats* __restrict__ stats) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = blockIdx.x * (int64_t)kFoldWarps + w;
     if (i >= Mh) return;
+    double* sv = reinterpret_cast<double*>(smem) + (size_t)w * kRowCap;
+    int32_t* sc = reinterpret_cast<int32_t*>(smem + (size_t)kFoldWarps * kRowCap * 8) + (size_t)w * kRowCap;
     const int sl = slice_of(sm.rows, sm.ns, i);
-    const int N = (int)(sm.N[sl + 1] - sm.N[sl]);
     const int col_base = (int)sm.cols[sl];  // folded columns of this slice start here
-    const int64_t e0 = hrp[i], e1 = hrp[i + 1];
+    const HalfRow h = stage_half_row(hrp, hcol, hval, i, (int)(sm.N[sl + 1] - sm.N[sl]), sc, sv, lane);
+    const int d0 = (int)((long long)lane * h.n / 32), d1 = (int)((long long)(lane + 1) * h.n / 32);
     float s1 = 0.f, s2 = 0.f;
     if constexpr (T::kQuant) {
         double m1 = 0.0, m2 = 0.0;
-        for_each_folded(hcol, hval, e0, e1, N, [&](int, double wd, double wr) {
+        merge_walk(h, d0, d1, [&](int, double wd, double wr) {
             m1 = fmax(m1, fabs(wd - wr));
             m2 = fmax(m2, fabs(wd + wr));
         });
-        s1 = (float)m1;
-        s2 = (float)m2;
-        scale[i] = make_float2(s1, s2);
+        s1 = (float)warp_max(m1);
+        s2 = (float)warp_max(m2);
+        if (lane == 0) scale[i] = make_float2(s1, s2);
     }
-    int32_t out = frp[i];
+    // Output position of this lane's first column: an exclusive scan of the lanes' counts.
+    int n = 0;
+    merge_walk(h, d0, d1, [&](int, double, double) { ++n; });
+    int incl = n;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int32_t first = frp[i];
+    int32_t out = first + incl - n;
     double R1 = 0.0, R2 = 0.0;
     long long zeros = 0;
-    for_each_folded(hcol, hval, e0, e1, N, [&](int c, double wd, double wr) {
+    merge_walk(h, d0, d1, [&](int c, double wd, double wr) {
         const double a1 = wd - wr, a2 = wd + wr;
         zeros += (a1 == 0.0);
         col[out] = col_base + c;
-        double d1, d2;
-        store_pair<T>(&val[out], a1, a2, s1, s2, d1, d2);
-        R1 += fabs(d1);
-        R2 += fabs(d2);
+        double q1, q2;
+        store_pair<T>(&val[out], a1, a2, s1, s2, q1, q2);
+        R1 += fabs(q1);
+        R2 += fabs(q2);
         ++out;
     });
-    Rsum[i] = make_double2(R1, R2);
-    using N2 = typename T::Norm2;
-    using NS = decltype(N2{}.x);
-    const double i1 = R1 > 0.0 ? 1.0 / R1 : 0.0, i2 = R2 > 0.0 ? 1.0 / R2 : 0.0;
-    invR[i] = N2{(NS)i1, (NS)i2};
-    // What the iteration applies: the row scale times 1/R, rounded once to FP32.
-    if constexpr (T::kQuant) wR[i] = make_float2((float)(i1 * (double)s1), (float)(i2 * (double)s2));
-    if (out == frp[i]) atomicAdd(reinterpret_cast<unsigned long long*>(&stats->empty_rows), 1ULL);
-    else atomicMax(&stats->max_row, out - frp[i]);
-    if (zeros) atomicAdd(reinterpret_cast<unsigned long long*>(&stats->exact_zeros), (unsigned long long)zeros);
-    if (i == Mh - 1) stats->S = frp[Mh];
+    R1 = warp_sum(R1);
+    R2 = warp_sum(R2);
+    zeros = warp_sum(zeros);
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane == 0) {
+        Rsum[i] = make_double2(R1, R2);
+        using N2 = typename T::Norm2;
+        using NS = decltype(N2{}.x);
+        const double i1 = R1 > 0.0 ? 1.0 / R1 : 0.0, i2 = R2 > 0.0 ? 1.0 / R2 : 0.0;
+        invR[i] = N2{(NS)i1, (NS)i2};
+        // What the iteration applies: the row scale times 1/R, rounded once to FP32.
+        if constexpr (T::kQuant) wR[i] = make_float2((float)(i1 * (double)s1), (float)(i2 * (double)s2));
+        if (total == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&stats->empty_rows), 1ULL);
+        else atomicMax(&stats->max_row, total);
+        if (zeros) atomicAdd(reinterpret_cast<unsigned long long*>(&stats->exact_zeros), (unsigned long long)zeros);
+        if (i == Mh - 1) stats->S = frp[Mh];
+    }
 }
 
 __global__ void csc_count_kernel(const int32_t* __restrict__ frp, int64_t Mh, int64_t cap,
@@ -255,14 +341,17 @@ __global__ void csc_count_kernel(const int32_t* __restrict__ frp, int64_t Mh, in
     atomicAdd(&ccnt[col[e]], 1);
 }
 
+// Place each folded entry in its column: one warp per row, lanes over the row's
+// entries. The order within a column is fixed afterwards by the sort.
 template <class T>
-__global__ void csc_place_kernel(int64_t Mh, const int32_t* __restrict__ frp, const int32_t* __restrict__ col,
-                                 const typename T::Pair* __restrict__ val, const int32_t* __restrict__ cp,
-                                 int32_t* __restrict__ cursor, int32_t* __restrict__ row,
-                                 typename T::Pair* __restrict__ valT) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kFoldWarps * 32) csc_place_kernel(
+    int64_t Mh, const int32_t* __restrict__ frp, const int32_t* __restrict__ col,
+    const typename T::Pair* __restrict__ val, const int32_t* __restrict__ cp, int32_t* __restrict__ cursor,
+    int32_t* __restrict__ row, typename T::Pair* __restrict__ valT) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = blockIdx.x * (int64_t)kFoldWarps + (threadIdx.x >> 5);
     if (i >= Mh) return;
-    for (int32_t e = frp[i]; e < frp[i + 1]; ++e) {
+    for (int32_t e = frp[i] + lane; e < frp[i + 1]; e += 32) {
         const int32_t c = col[e];
         const int32_t pos = cp[c] + atomicAdd(&cursor[c], 1);
         row[pos] = (int32_t)i;
@@ -270,48 +359,84 @@ __global__ void csc_place_kernel(int64_t Mh, const int32_t* __restrict__ frp, co
     }
 }
 
-// Sort each column's entries by row (insertion sort; columns are short), then
-// take the absolute column sums in that fixed order.
+// Sort each column's entries by row, then take the FP64 absolute column sums
+// in that order (lane-strided, fixed tree). One warp per column. A column of
+// up to kColCap entries is ranked in shared memory (rows within a column are
+// distinct, so an entry's rank is the number of smaller rows); a longer one is
+// sorted in place by one lane.
 template <class T>
-__global__ void csc_sort_colsum_kernel(int64_t Nh, const int32_t* __restrict__ cp, int32_t* __restrict__ row,
-                                       typename T::Pair* __restrict__ valT, const float2* __restrict__ scale,
-                                       double2* __restrict__ Csum, typename T::Norm2* __restrict__ invC,
-                                       float2* __restrict__ wC, FoldStats* __restrict__ stats) {
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kFoldWarps * 32) csc_sort_colsum_kernel(
+    int64_t Nh, const int32_t* __restrict__ cp, int32_t* __restrict__ row, typename T::Pair* __restrict__ valT,
+    const float2* __restrict__ scale, double2* __restrict__ Csum, typename T::Norm2* __restrict__ invC,
+    float2* __restrict__ wC, FoldStats* __restrict__ stats) {
+    using Pair = typename T::Pair;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t j = blockIdx.x * (int64_t)kFoldWarps + w;
     if (j >= Nh) return;
+    Pair* sv = reinterpret_cast<Pair*>(smem) + (size_t)w * 2 * kColCap;                 // unsorted, then sorted
+    int32_t* sr = reinterpret_cast<int32_t*>(smem + (size_t)kFoldWarps * 2 * kColCap * sizeof(Pair)) +
+                  (size_t)w * 2 * kColCap;
     const int32_t b = cp[j], e = cp[j + 1];
-    for (int32_t k = b + 1; k < e; ++k) {
-        const int32_t r = row[k];
-        const typename T::Pair v = valT[k];
-        int32_t m = k - 1;
-        while (m >= b && row[m] > r) {
-            row[m + 1] = row[m];
-            valT[m + 1] = valT[m];
-            --m;
+    const int n = e - b;
+    if (n <= kColCap) {
+        for (int t = lane; t < n; t += 32) {
+            sr[t] = row[b + t];
+            sv[t] = valT[b + t];
         }
-        row[m + 1] = r;
-        valT[m + 1] = v;
+        __syncwarp();
+        for (int t = lane; t < n; t += 32) {
+            const int32_t r = sr[t];
+            int rank = 0;
+            for (int u = 0; u < n; ++u) rank += sr[u] < r;
+            sr[kColCap + rank] = r;
+            sv[kColCap + rank] = sv[t];
+        }
+        __syncwarp();
+        for (int t = lane; t < n; t += 32) {
+            row[b + t] = sr[kColCap + t];
+            valT[b + t] = sv[kColCap + t];
+        }
+    } else if (lane == 0) {
+        for (int32_t k = b + 1; k < e; ++k) {
+            const int32_t r = row[k];
+            const Pair v = valT[k];
+            int32_t m = k - 1;
+            while (m >= b && row[m] > r) {
+                row[m + 1] = row[m];
+                valT[m + 1] = valT[m];
+                --m;
+            }
+            row[m + 1] = r;
+            valT[m + 1] = v;
+        }
     }
+    __syncwarp();
     double C1 = 0.0, C2 = 0.0;
-    for (int32_t k = b; k < e; ++k) {
+    for (int t = lane; t < n; t += 32) {
+        const bool st = n <= kColCap;
         typename T::Acc a1, a2;
-        T::decode(valT[k], a1, a2);
+        T::decode(st ? sv[kColCap + t] : valT[b + t], a1, a2);
         double d1 = a1, d2 = a2;
         if constexpr (T::kQuant) {
-            const float2 s = scale[row[k]];
-            d1 = (double)s.x * d1;
-            d2 = (double)s.y * d2;
+            const float2 sc = scale[st ? sr[kColCap + t] : row[b + t]];
+            d1 = (double)sc.x * d1;
+            d2 = (double)sc.y * d2;
         }
         C1 += fabs(d1);
         C2 += fabs(d2);
     }
-    Csum[j] = make_double2(C1, C2);
-    if (e > b) atomicMax(&stats->max_col, e - b);
-    using N2 = typename T::Norm2;
-    using NS = decltype(N2{}.x);
-    const double i1 = C1 > 0.0 ? 1.0 / C1 : 0.0, i2 = C2 > 0.0 ? 1.0 / C2 : 0.0;
-    invC[j] = N2{(NS)i1, (NS)i2};
-    if constexpr (T::kQuant) wC[j] = make_float2((float)i1, (float)i2);
+    C1 = warp_sum(C1);
+    C2 = warp_sum(C2);
+    if (lane == 0) {
+        Csum[j] = make_double2(C1, C2);
+        if (n > 0) atomicMax(&stats->max_col, n);
+        using N2 = typename T::Norm2;
+        using NS = decltype(N2{}.x);
+        const double i1 = C1 > 0.0 ? 1.0 / C1 : 0.0, i2 = C2 > 0.0 ? 1.0 / C2 : 0.0;
+        invC[j] = N2{(NS)i1, (NS)i2};
+        if constexpr (T::kQuant) wC[j] = make_float2((float)i1, (float)i2);
+    }
 }
 
 __global__ void nonempty_flags_kernel(int64_t n, const int32_t* __restrict__ ptr, int32_t* __restrict__ flags) {
@@ -360,11 +485,20 @@ int fold_typed(splitsart_system* s, cudaStream_t st) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(s->stats, 0, sizeof(FoldStats), st)) != cudaSuccess) return cuda_fail(e, "fold memset");
     const SliceMap sm = slice_map(s);
-    if (Mh > 0) fold_count_kernel<<<(unsigned)((Mh + 255) / 256), 256, 0, st>>>(Mh, sm, s->hrp, s->hcol, s->hval, s->cnt);
+    const size_t row_smem = (size_t)kFoldWarps * kRowCap * (8 + 4);
+    const size_t col_smem = (size_t)kFoldWarps * 2 * kColCap * (sizeof(Pair) + 4);
+    cudaFuncSetAttribute((const void*)fold_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem);
+    cudaFuncSetAttribute((const void*)fold_fill_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem);
+    cudaFuncSetAttribute((const void*)csc_sort_colsum_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)col_smem);
+    const unsigned row_blocks = (unsigned)((Mh + kFoldWarps - 1) / kFoldWarps);
+    const unsigned col_blocks = (unsigned)((Nh + kFoldWarps - 1) / kFoldWarps);
+    if (Mh > 0)
+        fold_count_kernel<<<row_blocks, kFoldWarps * 32, row_smem, st>>>(Mh, sm, s->hrp, s->hcol, s->hval, s->cnt);
     int rc = exclusive_scan(s->cnt, s->rp, s->scan_tmp, Mh, st);
     if (rc) return rc;
     if (Mh > 0)
-        fold_fill_kernel<T><<<(unsigned)((Mh + 127) / 128), 128, 0, st>>>(
+        fold_fill_kernel<T><<<row_blocks, kFoldWarps * 32, row_smem, st>>>(
             Mh, sm, s->hrp, s->hcol, s->hval, s->rp, s->col, (Pair*)s->val, s->Rsum, (N2*)s->invR, s->scale, s->wR,
             s->stats);
     rc = compact(s->rp, Mh, s->flags, s->cnt, s->scan_tmp, s->nzr, s->nzrp, s->zr, &s->stats->n_nzr,
@@ -381,10 +515,10 @@ int fold_typed(splitsart_system* s, cudaStream_t st) {
     if ((e = cudaMemsetAsync(s->cnt, 0, sizeof(int32_t) * (Nh + 1), st)) != cudaSuccess)
         return cuda_fail(e, "fold memset");
     if (Mh > 0)
-        csc_place_kernel<T><<<(unsigned)((Mh + 127) / 128), 128, 0, st>>>(Mh, s->rp, s->col, (const Pair*)s->val,
-                                                                          s->cp, s->cnt, s->row, (Pair*)s->valT);
+        csc_place_kernel<T><<<row_blocks, kFoldWarps * 32, 0, st>>>(Mh, s->rp, s->col, (const Pair*)s->val, s->cp,
+                                                                    s->cnt, s->row, (Pair*)s->valT);
     if (Nh > 0)
-        csc_sort_colsum_kernel<T><<<(unsigned)((Nh + 127) / 128), 128, 0, st>>>(
+        csc_sort_colsum_kernel<T><<<col_blocks, kFoldWarps * 32, col_smem, st>>>(
             Nh, s->cp, s->row, (Pair*)s->valT, s->scale, s->Csum, (N2*)s->invC, s->wC, s->stats);
     rc = compact(s->cp, Nh, s->flags, s->cnt, s->scan_tmp, s->nzc, s->nzcp, nullptr, &s->stats->n_nzc, nullptr, st);
     if (rc) return rc;
