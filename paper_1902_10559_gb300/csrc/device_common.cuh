@@ -161,7 +161,7 @@ struct LaunchCtl {
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).
 // ctl->bar_count only ever grows during a launch:
 // - thread 0 of each CTA adds 1 with a release reduction (a posted write that
-//   needs no round trip);
+//   needs no round trip; no separate fence);
 // - it then waits until the count reaches `target`, which is
 //   expected x (barrier index + 1).
 // The wait has a wall-clock limit and a spin cap. If either runs out, the wait
@@ -179,7 +179,8 @@ __device__ __forceinline__ bool grid_sync(LaunchCtl* ctl, unsigned target, unsig
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        __threadfence();
+        // The release orders this CTA's earlier writes: the CTA barrier above puts
+        // them before this thread's release, and release is cumulative.
         red_release_add(&ctl->bar_count, 1u);
         if (ld_acquire_gpu(&ctl->bar_count) < target) {
             const unsigned long long t0 = global_ns();
@@ -195,7 +196,8 @@ __device__ __forceinline__ bool grid_sync(LaunchCtl* ctl, unsigned target, unsig
                 __nanosleep(20);
             }
         }
-        __threadfence();  // acquire side: later loads of this CTA see the other CTAs' writes
+        // The acquire loads above, and the CTA barrier below, put the other CTAs'
+        // writes before every later load of this CTA.
         if (ld_volatile(&ctl->err) != 0) ok = 0;
         s_ok = ok;
     }

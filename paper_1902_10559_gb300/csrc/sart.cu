@@ -85,6 +85,22 @@ struct SartArgs {
     int* ndone;                // slices finished
 };
 
+// The joint stop test (one thread): rho = sqrt(rr / pp), 0 when pp = 0. CTA 0
+// records the result of the stopping pass. Returns 1 to stop.
+template <class A>
+__device__ __forceinline__ int stop_test(const A& a, int k, bool last, double trr, double tpp) {
+    const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
+    const bool stop = last || rho <= a.tol;
+    if (stop && blockIdx.x == 0) {
+        a.result->iters = k;
+        a.result->status = SPLITSART_OK;
+        a.result->rho = rho;
+        a.result->rr = trr;
+        a.result->pp = tpp;
+    }
+    return stop ? 1 : 0;
+}
+
 // The slice holding global index i (largest s with off[s] <= i).
 __device__ __forceinline__ int slice_index(const long long* off, int ns, long long i) {
     int lo = 0, hi = ns;
@@ -163,6 +179,7 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
     __shared__ int s_nrt, s_nct;
     __shared__ double s_red[2][32];
     __shared__ double s_tpp;
+    __shared__ int s_stop;
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -352,10 +369,12 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
                     if (__ldcg(&a.sl_solve[sl].done)) continue;
                     const double trr = warp_sum_range(a.rr_row, __ldg(a.sl_rows + sl), __ldg(a.sl_rows + sl + 1), lane);
                     const double tpp = __ldcg(&a.sl_solve[sl].pp);
-                    const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
-                    if (lane == 0 && (last || rho <= a.tol)) {
-                        a.sl_solve[sl] = SliceSolve{k, 1, rho, trr, tpp};
-                        atomicAdd(a.ndone, 1);
+                    if (lane == 0) {  // FP64 division and square root on one lane only
+                        const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
+                        if (last || rho <= a.tol) {
+                            a.sl_solve[sl] = SliceSolve{k, 1, rho, trr, tpp};
+                            atomicAdd(a.ndone, 1);
+                        }
                     }
                 }
             }
@@ -372,23 +391,13 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
             }
         } else if (last || (k % a.check_every == 0)) {
             // ---- stop test: every CTA sums the partials in the same order ----
+            // One thread decides, so the FP64 division and square root run once per CTA.
             if (wib == 0) {
-                const double t0 = grid_total(a.partials, gridDim.x, lane, 0);
-                if (lane == 0) s_red[0][0] = t0;
+                const double trr = grid_total(a.partials, gridDim.x, lane, 0);
+                if (lane == 0) s_stop = stop_test(a, k, last, trr, s_tpp);
             }
             __syncthreads();
-            const double trr = s_red[0][0], tpp = s_tpp;
-            const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
-            if (last || rho <= a.tol) {
-                if (blockIdx.x == 0 && tid == 0) {
-                    a.result->iters = k;
-                    a.result->status = SPLITSART_OK;
-                    a.result->rho = rho;
-                    a.result->rr = trr;
-                    a.result->pp = tpp;
-                }
-                return;
-            }
+            if (s_stop) return;
         }
 
         // ---- back-projection and update: f += lambda (A^T u) / C ----
@@ -537,15 +546,50 @@ __device__ __forceinline__ int2 resident_range(const int32_t* ptr, int n, int WE
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-// Largest item q in [0, n) with ptr[q] <= e (ptr in shared memory, ptr[0] = 0).
-__device__ __forceinline__ int item_of(const int* ptr, int n, int e) {
-    int lo = 0, hi = n;  // invariant: ptr[lo] <= e, answer in [lo, hi)
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (ptr[mid] <= e) lo = mid;
-        else hi = mid;
+// Gathers of NI items at once, lane-strided by W: one round issues up to UU
+// gathers per item from shared-memory indices, the next consumes them.
+template <class T, int NI, int UU>
+__device__ __forceinline__ void issue_round(const uint16_t* idx, const typename T::Vec2* src, const int (&lo)[NI],
+                                            const int (&hi)[NI], int base, int W, typename T::Vec2 (&g)[NI][UU]) {
+#pragma unroll
+    for (int k = 0; k < NI; ++k)
+#pragma unroll
+        for (int u = 0; u < UU; ++u) {
+            const int e = lo[k] + base + u * W;
+            if (e < hi[k]) g[k][u] = ldca(src + idx[e]);
+        }
+}
+template <class T, int NI, int UU>
+__device__ __forceinline__ void consume_round(const typename T::Pair* vals, const int (&lo)[NI], const int (&hi)[NI],
+                                              int base, int W, const typename T::Vec2 (&g)[NI][UU],
+                                              typename T::Acc (&s1)[NI], typename T::Acc (&s2)[NI]) {
+#pragma unroll
+    for (int k = 0; k < NI; ++k)
+#pragma unroll
+        for (int u = 0; u < UU; ++u) {
+            const int e = lo[k] + base + u * W;
+            if (e < hi[k]) {
+                typename T::Acc v1, v2;
+                T::decode(vals[e], v1, v2);
+                s1[k] += v1 * g[k][u].x;
+                s2[k] += v2 * g[k][u].y;
+            }
+        }
+}
+// All rounds from `base` on, for the items' remaining entries.
+template <class T, int NI, int UU>
+__device__ __forceinline__ void gather_rounds(const uint16_t* idx, const typename T::Pair* vals,
+                                              const typename T::Vec2* src, const int (&lo)[NI], const int (&hi)[NI],
+                                              int first, int base, int W, typename T::Acc (&s1)[NI],
+                                              typename T::Acc (&s2)[NI]) {
+    int n = 0;
+#pragma unroll
+    for (int k = 0; k < NI; ++k) n = max(n, hi[k] - lo[k]);
+    for (; base - first < n; base += UU * W) {
+        typename T::Vec2 g[NI][UU];
+        issue_round<T, NI, UU>(idx, src, lo, hi, base, W, g);
+        consume_round<T, NI, UU>(vals, lo, hi, base, W, g, s1, s2);
     }
-    return lo;
 }
 
 template <class T, int LPC>
@@ -555,13 +599,16 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
     using N2 = typename T::KNorm2;
     using Pair = typename T::Pair;
     using B = ResidentBytes<T>;
-    constexpr int U = B::kChunk;           // gathers in flight per lane and item
+    constexpr int U = B::kChunk;                   // forward: gathers in flight per lane and row
+    constexpr int NR = sizeof(V2) == 16 ? 2 : 3;   // forward: rows per warp in flight
+    constexpr int UB = sizeof(V2) == 16 ? 4 : 8;   // back: gathers in flight per lane and column
     constexpr int kGroupsPerWarp = 32 / LPC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int2 s_rows, s_cols;
     __shared__ double s_rrw[32];  // per warp: ||r||^2 of its rows
     __shared__ double2 s_pw[32];  // per warp, once: ||p||^2 over the empty rows, and over all rows
     __shared__ double s_tot[2];   // totals over the grid: ||r||^2 (per check), ||p||^2 (once)
+    __shared__ int s_stop;
     __shared__ double s_ppz;      // this CTA's ||p||^2 over its share of the empty rows
 
     const int tid = threadIdx.x;
@@ -682,36 +729,6 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
     }
     const double ppz = s_ppz;
 
-    // Gathers of one item's first U*W entries (lane-strided by W), and their use.
-    auto issue = [&](const uint16_t* idx, const V2* src, int lo, int hi, int first, int W, V2 (&g)[U]) {
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = lo + first + u * W;
-            if (e < hi) g[u] = ldca(src + idx[e]);
-        }
-    };
-    auto consume = [&](const Pair* vals, int lo, int hi, int first, int W, const V2 (&g)[U], Acc& s1, Acc& s2) {
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = lo + first + u * W;
-            if (e < hi) {
-                Acc v1, v2;
-                T::decode(vals[e], v1, v2);
-                s1 += v1 * g[u].x;
-                s2 += v2 * g[u].y;
-            }
-        }
-    };
-    // Entries beyond the first batch (items longer than U*W).
-    auto rest = [&](const uint16_t* idx, const Pair* vals, const V2* src, int lo, int hi, int first, int W, Acc& s1,
-                    Acc& s2) {
-        for (int base = first + U * W; lo + base - first < hi + W; base += U * W) {
-            V2 g[U];
-            issue(idx, src, lo, hi, base, W, g);
-            consume(vals, lo, hi, base, W, g, s1, s2);
-        }
-    };
-
     for (int k = 0;; ++k) {
         // ---- forward: r = p - A f, u = r / R, and the norm partials ----
         SqAcc<Acc> rr;  // lane 0 of each warp: its rows' ||r||^2
@@ -729,26 +746,28 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
             stcg(a.u12 + r_id[q], V2{r1 * ir.x, r2 * ir.y});
             rr.add(r1, r2);
         };
-        // Two rows per warp in flight: q and q + nwarps.
-        for (int q = wib; q < nr; q += 2 * nwarps) {
-            const int qb = q + nwarps;
-            const int loA = r_ptr[q], hiA = r_ptr[q + 1];
-            const int loB = qb < nr ? r_ptr[qb] : 0, hiB = qb < nr ? r_ptr[qb + 1] : 0;
-            V2 gA[U], gB[U];
-            issue(f_idx, a.f12, loA, hiA, lane, 32, gA);
-            issue(f_idx, a.f12, loB, hiB, lane, 32, gB);
-            Acc sA1 = 0, sA2 = 0, sB1 = 0, sB2 = 0;
-            consume(f_val, loA, hiA, lane, 32, gA, sA1, sA2);
-            consume(f_val, loB, hiB, lane, 32, gB, sB1, sB2);
-            rest(f_idx, f_val, a.f12, loA, hiA, lane, 32, sA1, sA2);
-            rest(f_idx, f_val, a.f12, loB, hiB, lane, 32, sB1, sB2);
-            sA1 = warp_sum(sA1);
-            sA2 = warp_sum(sA2);
-            sB1 = warp_sum(sB1);
-            sB2 = warp_sum(sB2);
+        // NR rows per warp in flight: q, q + nwarps, q + 2 nwarps, ...
+        for (int q = wib; q < nr; q += NR * nwarps) {
+            int lo[NR], hi[NR];
+            Acc s1[NR], s2[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                const int qk = q + k * nwarps;
+                lo[k] = qk < nr ? r_ptr[qk] : 0;
+                hi[k] = qk < nr ? r_ptr[qk + 1] : 0;
+                s1[k] = 0;
+                s2[k] = 0;
+            }
+            gather_rounds<T, NR, U>(f_idx, f_val, a.f12, lo, hi, lane, lane, 32, s1, s2);
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                s1[k] = warp_sum(s1[k]);
+                s2[k] = warp_sum(s2[k]);
+            }
             if (lane == 0) {
-                fin_row(q, sA1, sA2);
-                if (qb < nr) fin_row(qb, sB1, sB2);
+#pragma unroll
+                for (int k = 0; k < NR; ++k)
+                    if (q + k * nwarps < nr) fin_row(q + k * nwarps, s1[k], s2[k]);
             }
         }
         if (lane == 0) s_rrw[wib] = rr.sum();
@@ -774,46 +793,34 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
         bool first_pass = true;
         for (int g0 = wib * kGroupsPerWarp; g0 < nc || first_pass; g0 += stride) {
             const int qA = g0 + lane / LPC, qB = qA + nwarps * kGroupsPerWarp;
-            const int loA = qA < nc ? c_ptr[qA] : 0, hiA = qA < nc ? c_ptr[qA + 1] : 0;
-            const int loB = qB < nc ? c_ptr[qB] : 0, hiB = qB < nc ? c_ptr[qB + 1] : 0;
-            V2 gA[U], gB[U];
-            issue(b_idx, a.u12, loA, hiA, sub, LPC, gA);
-            issue(b_idx, a.u12, loB, hiB, sub, LPC, gB);
+            const int lo[2] = {qA < nc ? c_ptr[qA] : 0, qB < nc ? c_ptr[qB] : 0};
+            const int hi[2] = {qA < nc ? c_ptr[qA + 1] : 0, qB < nc ? c_ptr[qB + 1] : 0};
+            V2 g[2][UB];
+            issue_round<T, 2, UB>(b_idx, a.u12, lo, hi, sub, LPC, g);
             if (first_pass) {
                 first_pass = false;
                 if (check) {  // uniform over the CTA
+                    // One thread decides, so the FP64 division and square root run once per CTA.
                     if (wib == 0) {
-                        const double t0 = grid_total(a.partials, gridDim.x, lane, 0);
-                        if (lane == 0) s_tot[0] = t0;
+                        const double trr = grid_total(a.partials, gridDim.x, lane, 0);
+                        if (lane == 0) s_stop = stop_test(a, k, last, trr, s_tot[1]);
                     }
                     __syncthreads();
-                    const double trr = s_tot[0], tpp = s_tot[1];
-                    const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
-                    if (last || rho <= a.tol) {
-                        if (blockIdx.x == 0 && tid == 0) {
-                            a.result->iters = k;
-                            a.result->status = SPLITSART_OK;
-                            a.result->rho = rho;
-                            a.result->rr = trr;
-                            a.result->pp = tpp;
-                        }
-                        return;
-                    }
+                    if (s_stop) return;
                 }
                 if (g0 >= nc) break;  // uniform within the warp
             }
-            Acc bA1 = 0, bA2 = 0, bB1 = 0, bB2 = 0;
-            consume(b_val, loA, hiA, sub, LPC, gA, bA1, bA2);
-            consume(b_val, loB, hiB, sub, LPC, gB, bB1, bB2);
-            rest(b_idx, b_val, a.u12, loA, hiA, sub, LPC, bA1, bA2);
-            rest(b_idx, b_val, a.u12, loB, hiB, sub, LPC, bB1, bB2);
-            bA1 = warp_sum(bA1, LPC);
-            bA2 = warp_sum(bA2, LPC);
-            bB1 = warp_sum(bB1, LPC);
-            bB2 = warp_sum(bB2, LPC);
+            Acc b1[2] = {0, 0}, b2[2] = {0, 0};
+            consume_round<T, 2, UB>(b_val, lo, hi, sub, LPC, g, b1, b2);
+            gather_rounds<T, 2, UB>(b_idx, b_val, a.u12, lo, hi, sub, sub + UB * LPC, LPC, b1, b2);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                b1[k] = warp_sum(b1[k], LPC);
+                b2[k] = warp_sum(b2[k], LPC);
+            }
             if (sub == 0) {
-                if (qA < nc) fin_col(qA, bA1, bA2);
-                if (qB < nc) fin_col(qB, bB1, bB2);
+                if (qA < nc) fin_col(qA, b1[0], b2[0]);
+                if (qB < nc) fin_col(qB, b1[1], b2[1]);
             }
         }
         if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
@@ -869,6 +876,7 @@ __global__ void __launch_bounds__(512, 1) sart_rows_kernel(SartArgs<T> a) {
     constexpr int kRowChunk = 16;  // rows per scheduled chunk
     __shared__ double s_red[2][32];
     __shared__ double s_tpp;
+    __shared__ int s_stop;
 
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nwarps = blockDim.x >> 5, BD = blockDim.x;
     const int sub = lane % LPC;
@@ -1066,10 +1074,12 @@ __global__ void __launch_bounds__(512, 1) sart_rows_kernel(SartArgs<T> a) {
                     if (__ldcg(&a.sl_solve[sl].done)) continue;
                     const double trr = warp_sum_range(a.rr_row, __ldg(a.sl_rows + sl), __ldg(a.sl_rows + sl + 1), lane);
                     const double tpp = __ldcg(&a.sl_solve[sl].pp);
-                    const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
-                    if (lane == 0 && (last || rho <= a.tol)) {
-                        a.sl_solve[sl] = SliceSolve{k, 1, rho, trr, tpp};
-                        atomicAdd(a.ndone, 1);
+                    if (lane == 0) {  // FP64 division and square root on one lane only
+                        const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
+                        if (last || rho <= a.tol) {
+                            a.sl_solve[sl] = SliceSolve{k, 1, rho, trr, tpp};
+                            atomicAdd(a.ndone, 1);
+                        }
                     }
                 }
             }
@@ -1086,23 +1096,13 @@ __global__ void __launch_bounds__(512, 1) sart_rows_kernel(SartArgs<T> a) {
             }
         } else if (last || (k % a.check_every == 0)) {
             // ---- stop test: every CTA sums the partials in the same order ----
+            // One thread decides, so the FP64 division and square root run once per CTA.
             if (wib == 0) {
-                const double t0 = grid_total(a.partials, gridDim.x, lane, 0);
-                if (lane == 0) s_red[0][0] = t0;
+                const double trr = grid_total(a.partials, gridDim.x, lane, 0);
+                if (lane == 0) s_stop = stop_test(a, k, last, trr, s_tpp);
             }
             __syncthreads();
-            const double trr = s_red[0][0], tpp = s_tpp;
-            const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
-            if (last || rho <= a.tol) {
-                if (blockIdx.x == 0 && tid == 0) {
-                    a.result->iters = k;
-                    a.result->status = SPLITSART_OK;
-                    a.result->rho = rho;
-                    a.result->rr = trr;
-                    a.result->pp = tpp;
-                }
-                return;
-            }
+            if (s_stop) return;
         }
 
         // ---- back-projection and update: f += lambda (A^T u) / C ----
@@ -1190,10 +1190,11 @@ __global__ void __launch_bounds__(384, 1) sart_bulk_kernel(SartArgs<T> a, int te
     constexpr std::integral_constant<int, 2> kUD{};
     constexpr int kEB = 4 + (int)sizeof(Pair);  // staged bytes per entry
     constexpr int GPW = 32 / LPC;                // column groups per warp
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar[16][2];
     __shared__ double s_red[2][32];
     __shared__ double s_tpp;
+    __shared__ int s_stop;
 
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nwarps = blockDim.x >> 5, BD = blockDim.x;
     const int sub = lane % LPC;
@@ -1470,10 +1471,12 @@ __global__ void __launch_bounds__(384, 1) sart_bulk_kernel(SartArgs<T> a, int te
                     if (__ldcg(&a.sl_solve[sl].done)) continue;
                     const double trr = warp_sum_range(a.rr_row, __ldg(a.sl_rows + sl), __ldg(a.sl_rows + sl + 1), lane);
                     const double tpp = __ldcg(&a.sl_solve[sl].pp);
-                    const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
-                    if (lane == 0 && (last || rho <= a.tol)) {
-                        a.sl_solve[sl] = SliceSolve{k, 1, rho, trr, tpp};
-                        atomicAdd(a.ndone, 1);
+                    if (lane == 0) {  // FP64 division and square root on one lane only
+                        const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
+                        if (last || rho <= a.tol) {
+                            a.sl_solve[sl] = SliceSolve{k, 1, rho, trr, tpp};
+                            atomicAdd(a.ndone, 1);
+                        }
                     }
                 }
             }
@@ -1489,23 +1492,13 @@ __global__ void __launch_bounds__(384, 1) sart_bulk_kernel(SartArgs<T> a, int te
                 return;
             }
         } else if (last || (k % a.check_every == 0)) {
+            // One thread decides, so the FP64 division and square root run once per CTA.
             if (wib == 0) {
-                const double t0 = grid_total(a.partials, gridDim.x, lane, 0);
-                if (lane == 0) s_red[0][0] = t0;
+                const double trr = grid_total(a.partials, gridDim.x, lane, 0);
+                if (lane == 0) s_stop = stop_test(a, k, last, trr, s_tpp);
             }
             __syncthreads();
-            const double trr = s_red[0][0], tpp = s_tpp;
-            const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
-            if (last || rho <= a.tol) {
-                if (blockIdx.x == 0 && tid == 0) {
-                    a.result->iters = k;
-                    a.result->status = SPLITSART_OK;
-                    a.result->rho = rho;
-                    a.result->rr = trr;
-                    a.result->pp = tpp;
-                }
-                return;
-            }
+            if (s_stop) return;
         }
 
         // ---- back-projection and update: f += lambda (A^T u) / C ----
