@@ -85,6 +85,35 @@ struct SartArgs {
     int* ndone;                // slices finished
 };
 
+// Per-slice stop tests of a batch: one CTA per slice sums the slice's per-row
+// residual^2 (thread-strided, then a fixed tree), and one thread decides.
+// red: 32 doubles of shared scratch. Called by every thread of the CTA.
+template <class A>
+__device__ void slice_stop_tests(const A& a, int k, bool last, double* red) {
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int sl = blockIdx.x; sl < a.ns; sl += gridDim.x) {
+        if (__ldcg(&a.sl_solve[sl].done)) continue;  // uniform over the CTA
+        double t = 0.0;
+        for (long long i = __ldg(a.sl_rows + sl) + tid; i < __ldg(a.sl_rows + sl + 1); i += blockDim.x)
+            t += __ldcg(a.rr_row + i);
+        t = warp_sum(t);
+        if (lane == 0) red[wib] = t;
+        __syncthreads();
+        if (wib == 0) {
+            const double trr = warp_sum(lane < nwarps ? red[lane] : 0.0);
+            if (lane == 0) {
+                const double tpp = __ldcg(&a.sl_solve[sl].pp);
+                const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
+                if (last || rho <= a.tol) {
+                    a.sl_solve[sl] = SliceSolve{k, 1, rho, trr, tpp};
+                    atomicAdd(a.ndone, 1);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // The joint stop test (one thread): rho = sqrt(rr / pp), 0 when pp = 0. CTA 0
 // records the result of the stopping pass. Returns 1 to stop.
 template <class A>
@@ -110,13 +139,6 @@ __device__ __forceinline__ int slice_index(const long long* off, int ns, long lo
         else hi = mid;
     }
     return lo;
-}
-
-// One warp: sum of v[lo..hi) in a fixed order (lane-strided, then a shuffle tree).
-__device__ __forceinline__ double warp_sum_range(const double* v, long long lo, long long hi, int lane) {
-    double t = 0.0;
-    for (long long i = lo + lane; i < hi; i += 32) t += __ldcg(v + i);
-    return warp_sum(t);
 }
 
 // Warp-cooperative search: the first q in [lo, hi] with ptr[q] >= t, where
@@ -363,21 +385,8 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
 
         const bool last = (k >= a.max_iters);
         if constexpr (kBatch) {
-            // ---- per-slice stop tests: one warp per slice, fixed order ----
-            if (last || (k % a.check_every == 0)) {
-                for (int sl = gw; sl < a.ns; sl += nw_grid) {
-                    if (__ldcg(&a.sl_solve[sl].done)) continue;
-                    const double trr = warp_sum_range(a.rr_row, __ldg(a.sl_rows + sl), __ldg(a.sl_rows + sl + 1), lane);
-                    const double tpp = __ldcg(&a.sl_solve[sl].pp);
-                    if (lane == 0) {  // FP64 division and square root on one lane only
-                        const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
-                        if (last || rho <= a.tol) {
-                            a.sl_solve[sl] = SliceSolve{k, 1, rho, trr, tpp};
-                            atomicAdd(a.ndone, 1);
-                        }
-                    }
-                }
-            }
+            // ---- per-slice stop tests: one CTA per slice, fixed order ----
+            if (last || (k % a.check_every == 0)) slice_stop_tests(a, k, last, s_red[0]);
             if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
             if (ld_volatile(a.ndone) >= a.ns) {
                 if (blockIdx.x == 0 && tid == 0) {
@@ -1068,21 +1077,8 @@ __global__ void __launch_bounds__(512, 1) sart_rows_kernel(SartArgs<T> a) {
 
         const bool last = (k >= a.max_iters);
         if constexpr (kBatch) {
-            // ---- per-slice stop tests: one warp per slice, fixed order ----
-            if (last || (k % a.check_every == 0)) {
-                for (int sl = gw; sl < a.ns; sl += nw_grid) {
-                    if (__ldcg(&a.sl_solve[sl].done)) continue;
-                    const double trr = warp_sum_range(a.rr_row, __ldg(a.sl_rows + sl), __ldg(a.sl_rows + sl + 1), lane);
-                    const double tpp = __ldcg(&a.sl_solve[sl].pp);
-                    if (lane == 0) {  // FP64 division and square root on one lane only
-                        const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
-                        if (last || rho <= a.tol) {
-                            a.sl_solve[sl] = SliceSolve{k, 1, rho, trr, tpp};
-                            atomicAdd(a.ndone, 1);
-                        }
-                    }
-                }
-            }
+            // ---- per-slice stop tests: one CTA per slice, fixed order ----
+            if (last || (k % a.check_every == 0)) slice_stop_tests(a, k, last, s_red[0]);
             if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
             if (ld_volatile(a.ndone) >= a.ns) {
                 if (blockIdx.x == 0 && tid == 0) {
@@ -1466,20 +1462,7 @@ __global__ void __launch_bounds__(384, 1) sart_bulk_kernel(SartArgs<T> a, int te
 
         const bool last = (k >= a.max_iters);
         if constexpr (kBatch) {
-            if (last || (k % a.check_every == 0)) {
-                for (int sl = gw; sl < a.ns; sl += nw_grid) {
-                    if (__ldcg(&a.sl_solve[sl].done)) continue;
-                    const double trr = warp_sum_range(a.rr_row, __ldg(a.sl_rows + sl), __ldg(a.sl_rows + sl + 1), lane);
-                    const double tpp = __ldcg(&a.sl_solve[sl].pp);
-                    if (lane == 0) {  // FP64 division and square root on one lane only
-                        const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
-                        if (last || rho <= a.tol) {
-                            a.sl_solve[sl] = SliceSolve{k, 1, rho, trr, tpp};
-                            atomicAdd(a.ndone, 1);
-                        }
-                    }
-                }
-            }
+            if (last || (k % a.check_every == 0)) slice_stop_tests(a, k, last, s_red[0]);
             if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
             if (ld_volatile(a.ndone) >= a.ns) {
                 if (blockIdx.x == 0 && tid == 0) {
@@ -1571,12 +1554,14 @@ constexpr int default_tile_entries() {
     return sizeof(typename T::Vec2) == 16 ? 8192 : 12288;
 }
 
-// Row-streaming kernel: entries in flight per lane and item (FP64 pairs are
-// twice as wide, so they keep fewer in flight).
+// Row-streaming kernel: entries in flight per lane and item. Five per row
+// cover most rows of the batch (about 136 entries) in one round; FP64 pairs
+// are twice as wide, so they keep fewer in flight.
 template <class T, int LPC>
 void* rows_kernel(bool batch) {
-    constexpr int kU = sizeof(typename T::Vec2) == 16 ? 2 : 4;
-    return batch ? (void*)sart_rows_kernel<T, LPC, true, kU, kU> : (void*)sart_rows_kernel<T, LPC, false, kU, kU>;
+    constexpr bool kWide = sizeof(typename T::Vec2) == 16;
+    constexpr int kUF = kWide ? 2 : 5, kUB = kWide ? 2 : 4;
+    return batch ? (void*)sart_rows_kernel<T, LPC, true, kUF, kUB> : (void*)sart_rows_kernel<T, LPC, false, kUF, kUB>;
 }
 
 template <class T>
