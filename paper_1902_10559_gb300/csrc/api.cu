@@ -336,10 +336,9 @@ extern "C" int splitsart_refold(splitsart_system* s, void* stream) {
 
 extern "C" void splitsart_system_destroy(splitsart_system* s) {
     if (!s) return;
-    if (s->base) {
-        cudaStreamSynchronize(s->last);
-        cudaFree(s->base);
-    }
+    if (s->base || s->res_alloc) cudaStreamSynchronize(s->last);
+    if (s->base) cudaFree(s->base);
+    if (s->res_alloc) cudaFree(s->res_alloc);
     delete s;
 }
 

@@ -35,7 +35,10 @@
 // normalisers use the read-only path.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
+#include <initializer_list>
 #include <mutex>
+#include <vector>
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -83,6 +86,10 @@ struct SartArgs {
     SliceSolve* sl_solve;      // [ns]
     double* rr_row;            // [Mh] per-row residual^2
     int* ndone;                // slices finished
+    // Resident kernel only: the row plan (null: contiguous row ranges).
+    const int32_t* res_rows;
+    const int32_t* res_off;
+    const int32_t* res_loc;
 };
 
 // Per-slice stop tests of a batch: one CTA per slice sums the slice's per-row
@@ -638,9 +645,17 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
         if (lane == 0) s_cols = r;
     }
     __syncthreads();
-    const int q0 = s_rows.x, nr = s_rows.y - s_rows.x;
+    // Rows: the host's plan (contiguous ranges balanced by time), or a range
+    // balanced by bytes.
+    const bool planned = a.res_rows != nullptr;
+    const int rg0 = planned ? __ldg(a.res_off + blockIdx.x) : 0;
+    const int q0 = planned ? 0 : s_rows.x;
+    const int nr = planned ? __ldg(a.res_off + blockIdx.x + 1) - rg0 : s_rows.y - s_rows.x;
+    const int32_t* loc = planned ? a.res_loc + rg0 + blockIdx.x : nullptr;
+    auto row_pos = [&](int q) { return planned ? __ldg(a.res_rows + rg0 + q) : q0 + q; };  // compacted position
     const int c0 = s_cols.x, nc = s_cols.y - s_cols.x;
-    const int fea = __ldg(a.nzrp + q0), nfe = __ldg(a.nzrp + q0 + nr) - fea;
+    const int fea = planned ? 0 : __ldg(a.nzrp + q0);
+    const int nfe = planned ? __ldg(loc + nr) : __ldg(a.nzrp + q0 + nr) - fea;
     const int bea = __ldg(a.nzcp + c0), nbe = __ldg(a.nzcp + c0 + nc) - bea;
 
     size_t off = 0;
@@ -677,13 +692,24 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
         grid_sync(a.ctl, a.expected, a.timeout_ns, 1);
         return;
     }
-    for (int e = tid; e < nfe; e += BD) {
-        f_val[e] = ldg(a.val + fea + e);
-        f_idx[e] = (uint16_t)__ldg(a.col + fea + e);
+    if (planned) {
+        for (int q = wib; q < nr; q += nwarps) {  // one warp per row
+            const int src = __ldg(a.nzrp + row_pos(q)), len = __ldg(a.nzrp + row_pos(q) + 1) - src;
+            const int dst = __ldg(loc + q);
+            for (int t = lane; t < len; t += 32) {
+                f_val[dst + t] = ldg(a.val + src + t);
+                f_idx[dst + t] = (uint16_t)__ldg(a.col + src + t);
+            }
+        }
+    } else {
+        for (int e = tid; e < nfe; e += BD) {
+            f_val[e] = ldg(a.val + fea + e);
+            f_idx[e] = (uint16_t)__ldg(a.col + fea + e);
+        }
     }
     for (int q = tid; q < nr; q += BD) {
-        const int i = __ldg(a.nzr + q0 + q);
-        r_ptr[q] = __ldg(a.nzrp + q0 + q) - fea;
+        const int i = __ldg(a.nzr + row_pos(q));
+        r_ptr[q] = planned ? __ldg(loc + q) : __ldg(a.nzrp + q0 + q) - fea;
         r_id[q] = i;
         r_p[q] = ldg(a.p12 + i);
         r_ir[q] = ldg(a.invR + i);
@@ -713,7 +739,7 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
             tz += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
         }
         for (int q = tid; q < nr; q += BD) {
-            const V2 p = ldg(a.p12 + __ldg(a.nzr + q0 + q));
+            const V2 p = ldg(a.p12 + __ldg(a.nzr + row_pos(q)));
             ta += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
         }
         ta += tz;
@@ -1603,6 +1629,82 @@ void fill_args(SartArgs<T>& a, splitsart_system* s, const void* p12, void* f12, 
     a.sl_solve = s->sl_solve;
     a.rr_row = s->rr_row;
     a.ndone = s->ndone;
+    a.res_rows = nullptr;
+    a.res_off = nullptr;
+    a.res_loc = nullptr;
+}
+
+// Row plan of the resident kernel for a grid of G CTAs: contiguous ranges of
+// the non-empty rows, balanced by time rather than by bytes. A warp step costs
+// about one gather round trip whatever its rows' lengths, so a CTA's forward
+// pass takes time in proportion to its rows as well as to its entries; on the
+// realistic slice a byte-balanced split gave CTAs from 29 to 134 rows and
+// forward passes from 2.8 to 6.6 us, with every CTA then waiting for the
+// slowest at the grid barrier. Here each row weighs row_weight entries more
+// than its length. Ranges keep the rows' order, so neighbouring rays (which
+// gather neighbouring voxels) stay together. Built on the first resident solve
+// and kept: the rows do not change across refolds.
+template <class T>
+int resident_plan(splitsart_system* s, const FoldStats& fs, int G, int row_weight, cudaStream_t st) {
+    if (s->res_G == G && s->res_weight == row_weight) return SPLITSART_OK;
+    using B = ResidentBytes<T>;
+    const int n = fs.n_nzr;
+    if (s->res_ptr.size() != (size_t)n + 1) {
+        std::vector<int32_t> ptr((size_t)n + 1);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ptr.data(), s->nzrp, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "solve: read the row pointers for the resident plan");
+        s->res_ptr.swap(ptr);
+    }
+    const std::vector<int32_t>& ptr = s->res_ptr;
+    // Prefix of the time weights; CTA b takes the rows whose prefix falls in [b W/G, (b+1) W/G).
+    std::vector<long long> cum((size_t)n + 1, 0);
+    for (int q = 0; q < n; ++q) cum[q + 1] = cum[q] + (ptr[q + 1] - ptr[q]) + row_weight;
+    const long long total = cum[n];
+    std::vector<int32_t> rows((size_t)n), off((size_t)G + 1), loc;
+    loc.reserve((size_t)n + G);
+    for (int q = 0; q < n; ++q) rows[q] = q;
+    long long worst = 0;
+    int q = 0;
+    for (int b = 0; b < G; ++b) {
+        const long long lim = total * (b + 1) / G;
+        off[b] = q;
+        int32_t run = 0;
+        long long bytes = 0;
+        const int q_end = (b == G - 1) ? n : (int)(std::lower_bound(cum.begin() + q, cum.end(), lim) - cum.begin());
+        for (; q < q_end && q < n; ++q) {
+            loc.push_back(run);
+            const int len = ptr[q + 1] - ptr[q];
+            run += len;
+            bytes += (long long)B::kEntry * len + B::kRow;
+        }
+        loc.push_back(run);
+        worst = std::max(worst, bytes);
+    }
+    off[G] = n;
+    cudaError_t e;
+    if (s->res_alloc) {
+        cudaFree(s->res_alloc);
+        s->res_alloc = nullptr;
+        s->res_G = 0;
+    }
+    const size_t bytes = sizeof(int32_t) * (rows.size() + off.size() + loc.size());
+    if ((e = cudaMalloc(&s->res_alloc, bytes > 0 ? bytes : 4)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SPLITSART_ERR_NOMEM, "solve: cudaMalloc of the resident plan (%zu bytes) failed", bytes);
+    }
+    s->res_rows = (int32_t*)s->res_alloc;
+    s->res_off = s->res_rows + rows.size();
+    s->res_loc = s->res_off + off.size();
+    e = cudaMemcpy(s->res_rows, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->res_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->res_loc, loc.data(), sizeof(int32_t) * loc.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "solve: upload the resident plan");
+    s->res_G = G;
+    s->res_weight = row_weight;
+    s->res_row_bytes = worst;
+    return SPLITSART_OK;
 }
 
 // Upper bound of one CTA's resident shared-memory bytes for a grid of G CTAs.
@@ -1641,10 +1743,28 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
     const long long res_avail = (long long)smem_optin - (long long)fa.sharedSizeBytes -
                                 (long long)ResidentBytes<T>::kThread * res_threads - 32;
     const bool batch = s->ns > 1;
-    const bool res_ok = !batch && s->Mh <= 65536 && s->Nh <= 65536 && resident_bound<T>(fs, nsm) <= res_avail;
+    const bool res_shape = !batch && s->Mh <= 65536 && s->Nh <= 65536;
+    long long need = resident_bound<T>(fs, nsm);
+    bool use_plan = false;
+    if (res_shape && (o.kernel == 0 || o.kernel == 2)) {
+        // Heaviest row weight whose plan fits in shared memory (weight 0 balances entries alone).
+        using B = ResidentBytes<T>;
+        const long long Wc = (long long)B::kEntry * fs.S + (long long)B::kCol * fs.n_nzc;
+        const long long col_part = (Wc + nsm - 1) / nsm + (long long)B::kEntry * fs.max_col + B::kCol + B::kSlack;
+        for (int w : {160, 80, 40, 0}) {
+            rc = resident_plan<T>(s, fs, nsm, w, st);
+            if (rc) return rc;
+            if (s->res_row_bytes + col_part <= res_avail) {
+                use_plan = true;
+                need = s->res_row_bytes + col_part;
+                break;
+            }
+        }
+    }
+    const bool res_ok = res_shape && need <= res_avail;
     if (o.kernel == 2 && !res_ok)
         return fail(SPLITSART_ERR_ARG, "solve: the system does not fit in shared memory (need %lld of %lld bytes per SM)",
-                    resident_bound<T>(fs, nsm), res_avail);
+                    need, res_avail);
     const bool use_res = o.kernel == 2 || (o.kernel == 0 && res_ok);
     const bool use_rows = o.kernel == 3 || (o.kernel == 0 && !res_ok);
     const bool use_bulk = o.kernel == 4;
@@ -1700,6 +1820,11 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
         if (grid > kMaxCtas) grid = kMaxCtas;
     }
     fill_args<T>(a, s, p12, f12, o, (unsigned)grid);
+    if (use_res && use_plan) {
+        a.res_rows = s->res_rows;
+        a.res_off = s->res_off;
+        a.res_loc = s->res_loc;
+    }
 
     if ((e = cudaMemsetAsync(s->ctl, 0, sizeof(LaunchCtl), st)) != cudaSuccess) return cuda_fail(e, "solve: memset");
     // A result the launch never writes (a timeout) reads back as iters = -1.

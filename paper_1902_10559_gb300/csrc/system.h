@@ -124,6 +124,17 @@ struct splitsart_system {
     splitsart::LaunchCtl* ctl = nullptr;
     splitsart::SolveResultDev* result = nullptr;
     void* base = nullptr;            // single device allocation holding all of the above
+
+    // Row plan of the shared-memory-resident solve, built on its first use for a
+    // grid of res_G CTAs and a row weight (the rows do not change across refolds).
+    int res_G = 0;
+    int res_weight = -1;
+    std::vector<int32_t> res_ptr;  // host copy of the compacted row pointers
+    int32_t* res_rows = nullptr;   // [n_nzr] compacted row positions, in CTA order
+    int32_t* res_off = nullptr;    // [G + 1] start of each CTA's group in res_rows
+    int32_t* res_loc = nullptr;    // [n_nzr + G] per group: local entry offsets of its rows, then its total
+    long long res_row_bytes = 0;   // the largest CTA's shared-memory bytes for its rows
+    void* res_alloc = nullptr;     // device allocation of the plan
 };
 
 namespace splitsart {
