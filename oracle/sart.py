@@ -90,6 +90,24 @@ def split_sart(A1, A2, p1, p2, lam: float, max_iters: int, tol: float = 0.0,
     return out
 
 
+def sart_fixed(B, q, lam: float, iters: int, f0=None):
+    """SART on one split system for a fixed number of iterations (no stop test).
+
+    This is one of the two independent solves that the method runs in parallel
+    (Section 2): with tol = 0 the joint stopping rule never fires, so split_sart
+    is exactly this function applied to (A1, p1) and to (A2, p2).
+    """
+    B = sp.csr_matrix(B, dtype=float)
+    q = np.asarray(q, dtype=float)
+    R, C = normalisers(B)
+    iR, iC = _safe_inv(R), _safe_inv(C)
+    Bt = B.T.tocsr()
+    f = np.zeros(B.shape[1]) if f0 is None else np.array(f0, dtype=float)
+    for _ in range(iters):
+        f = f + lam * (Bt @ ((q - B @ f) * iR)) * iC
+    return f
+
+
 def split_sart_dense(A1, A2, p1, p2, lam: float, max_iters: int, tol: float = 0.0,
                      f1_0=None, f2_0=None):
     """Dense matrix form of ``split_sart``, written independently as a cross-check.

@@ -138,3 +138,13 @@ def test_split_and_full_matrix_sizes(tiny_system):
     S = split.folded_pattern_size(A)
     assert A.nnz / 2 * 0.5 <= S <= A.nnz / 2
     assert sp.csr_matrix(A1).nnz <= S
+
+
+def test_fixed_iterations_per_system_equal_the_joint_solve():
+    """Section 2's independence: without a stop test the two systems do not interact."""
+    rng = np.random.default_rng(7)
+    A1, A2 = rng.standard_normal((3, 4)), np.abs(rng.standard_normal((3, 4)))
+    p1, p2 = rng.standard_normal(3), rng.standard_normal(3)
+    ref = sart.split_sart(A1, A2, p1, p2, 0.9, 37)
+    assert np.array_equal(sart.sart_fixed(A1, p1, 0.9, 37), ref["f1"])
+    assert np.array_equal(sart.sart_fixed(A2, p2, 0.9, 37), ref["f2"])
