@@ -306,12 +306,14 @@ int create_system(const splitsart_geometry* const* geoms, int ns, int dtype, cud
 }  // namespace
 
 extern "C" int splitsart_fold_system(const splitsart_geometry* g, int dtype, void* stream, splitsart_system** out) {
+    splitsart::NvtxRange nvtx_range("splitsart_fold_system");
     if (!g) return fail(SPLITSART_ERR_ARG, "fold_system: NULL geometry");
     return create_system(&g, 1, dtype, (cudaStream_t)stream, out);
 }
 
 extern "C" int splitsart_fold_batch(const splitsart_geometry* const* geoms, int nslices, int dtype, void* stream,
                                     splitsart_system** out) {
+    splitsart::NvtxRange nvtx_range("splitsart_fold_batch");
     return create_system(geoms, nslices, dtype, (cudaStream_t)stream, out);
 }
 
@@ -328,6 +330,7 @@ extern "C" int splitsart_system_slices(const splitsart_system* s, int64_t* M_off
 }
 
 extern "C" int splitsart_refold(splitsart_system* s, void* stream) {
+    splitsart::NvtxRange nvtx_range("splitsart_refold");
     if (!s) return fail(SPLITSART_ERR_ARG, "refold: NULL system");
     s->last = (cudaStream_t)stream;
     s->S = -1;
@@ -415,6 +418,7 @@ extern "C" int splitsart_system_export_csc(splitsart_system* s, int64_t* cp_h, i
 }
 
 extern "C" int splitsart_fold_rhs(const splitsart_system* s, const void* p, void* p12, void* stream) {
+    splitsart::NvtxRange nvtx_range("splitsart_fold_rhs");
     if (!s || (s->Mh > 0 && (!p || !p12))) return fail(SPLITSART_ERR_ARG, "fold_rhs: NULL argument");
     const_cast<splitsart_system*>(s)->last = (cudaStream_t)stream;
     return run_fold_rhs(s, p, p12, (cudaStream_t)stream);
@@ -432,6 +436,7 @@ static int check_layout(const splitsart_system* s, int layout, const char* who) 
 }
 
 extern "C" int splitsart_fold_image(const splitsart_system* s, const void* f, int layout, void* f12, void* stream) {
+    splitsart::NvtxRange nvtx_range("splitsart_fold_image");
     if (!s || (s->Nh > 0 && (!f || !f12))) return fail(SPLITSART_ERR_ARG, "fold_image: NULL argument");
     int rc = check_layout(s, layout, "fold_image");
     if (rc) return rc;
@@ -440,6 +445,7 @@ extern "C" int splitsart_fold_image(const splitsart_system* s, const void* f, in
 }
 
 extern "C" int splitsart_recombine(const splitsart_system* s, const void* f12, void* f, int layout, void* stream) {
+    splitsart::NvtxRange nvtx_range("splitsart_recombine");
     if (!s || (s->Nh > 0 && (!f || !f12))) return fail(SPLITSART_ERR_ARG, "recombine: NULL argument");
     int rc = check_layout(s, layout, "recombine");
     if (rc) return rc;
@@ -448,6 +454,7 @@ extern "C" int splitsart_recombine(const splitsart_system* s, const void* f12, v
 }
 
 extern "C" int splitsart_project(splitsart_system* s, const void* f, int layout, void* p, void* stream) {
+    splitsart::NvtxRange nvtx_range("splitsart_project");
     if (!s || !f || !p) return fail(SPLITSART_ERR_ARG, "project: NULL argument");
     int rc = check_layout(s, layout, "project");
     if (rc) return rc;
@@ -457,6 +464,7 @@ extern "C" int splitsart_project(splitsart_system* s, const void* f, int layout,
 
 extern "C" int splitsart_solve(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts* o,
                                void* stream) {
+    splitsart::NvtxRange nvtx_range("splitsart_solve");
     if (!s || !o) return fail(SPLITSART_ERR_ARG, "solve: NULL argument");
     if ((s->Mh > 0 && !p12) || (s->Nh > 0 && !f12)) return fail(SPLITSART_ERR_ARG, "solve: NULL vector");
     if (o->max_iters < 0 || o->max_iters > 500000)

@@ -2,6 +2,8 @@
 // channel and the geometry handle.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstdarg>
 #include <cstdint>
 #include <string>
@@ -10,6 +12,16 @@
 #include "../../include/splitsart.h"
 
 namespace splitsart {
+
+// An NVTX range for the duration of a C-ABI call, so that a profiler's
+// timeline shows the library's steps (fold, solve, recombine, ...). Without a
+// tool attached a push/pop costs next to nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Record a failure for splitsart_last_error() and return `code`.
 int fail(int code, const char* fmt, ...);

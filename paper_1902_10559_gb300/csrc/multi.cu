@@ -390,6 +390,7 @@ extern "C" int splitsart_pick_start(const splitsart_system* s, int nrhs, const v
 extern "C" int splitsart_solve_multi(splitsart_system* s, int nrhs, const void* p12_dev, void* f12_dev,
                                      const splitsart_solve_opts* o, int rhs_per_cta, splitsart_solve_info* info_dev,
                                      void* stream) {
+    splitsart::NvtxRange nvtx_range("splitsart_solve_multi");
     if (!s || !o || !p12_dev || !f12_dev || !info_dev) return fail(SPLITSART_ERR_ARG, "solve_multi: NULL argument");
     if (nrhs < 1) return fail(SPLITSART_ERR_ARG, "solve_multi: nrhs must be >= 1");
     if (s->ns != 1) return fail(SPLITSART_ERR_ARG, "solve_multi: needs a single-slice system");

@@ -2008,6 +2008,7 @@ extern "C" int splitsart_solve_static(int64_t Mh, int64_t Nh, const int32_t* rp_
                                       const void* valT_dev, const void* invR_dev, const void* invC_dev,
                                       const void* p12_dev, void* f12_dev, const splitsart_solve_opts* opts,
                                       splitsart_solve_info* info_dev, void* stream) {
+    splitsart::NvtxRange nvtx_range("splitsart_solve_static");
     using namespace splitsart;
     if (!opts || !info_dev || !rp_dev || !cp_dev || !p12_dev || !f12_dev || !invR_dev || !invC_dev)
         return fail(SPLITSART_ERR_ARG, "solve_static: NULL argument");

@@ -48,6 +48,7 @@ class WarmStart:
         self.chunk = chunk
         self.vec = ss.fold_batch([self.geom] * chunk, ss.F32)  # [chunk][...] layouts for the vector folds
         self.cnn = ss.Cnn(g.nz, g.nx, max_batch, cnn_initial_params() if params is None else params)
+        self.steps = 0  # Adam steps taken
         if mode:
             self.cnn.set_mode(mode)
         self.dev = torch.device("cuda")
@@ -122,7 +123,9 @@ class WarmStart:
         return x, t
 
     # ---- 2. training ----
-    def train(self, x, t, epochs=10, batch=64, lr=1e-3, seed=0, log_every=0):
+    def train(self, x, t, epochs=10, batch=64, lr=1e-3, seed=0, log_every=0, checkpoint=None):
+        """Adam on mini-batches. With ``checkpoint`` (a path), the weights, the
+        Adam moments and the step count are written there after every epoch."""
         import torch
         n = x.shape[0]
         rng = np.random.default_rng(seed)
@@ -138,10 +141,24 @@ class WarmStart:
                 self.cnn.train_step(xb, tb, lr=lr, loss=loss)
                 acc += loss.double()
                 steps += 1
+            self.steps += steps
             hist.append(float(acc.item() / max(steps, 1)))
+            if checkpoint:
+                self.save(checkpoint, epoch=ep + 1, loss=hist[-1])
             if log_every and (ep + 1) % log_every == 0:
                 print(f"epoch {ep + 1}: mean loss {hist[-1]:.4e}", flush=True)
         return hist
+
+    def save(self, path, **meta):
+        """Write the network's weights, Adam moments and step count to ``path`` (.npz)."""
+        p, m, v = self.cnn.params(moments=True)
+        np.savez(path, params=p, m=m, v=v, step=np.int64(self.steps), **{k: np.asarray(x) for k, x in meta.items()})
+
+    def load(self, path):
+        """Resume from a file written by ``save``: training continues exactly where it stopped."""
+        z = np.load(path)
+        self.steps = int(z["step"])
+        self.cnn.set_params(z["params"], z["m"], z["v"], step=self.steps)
 
     def predict(self, x):
         import torch

@@ -67,3 +67,19 @@ def test_oracle_judges_warm_start_residual(ws):
         f = ogeo.image_to_snake(TINY, img[r])
         rho = osplit.relative_residual(A, f, p[r].double().cpu().numpy())
         assert rho <= 2e-3 * 1.01, (r, rho)
+
+
+@pytest.mark.gpu
+def test_training_checkpoint_resumes_exactly(tmp_path):
+    """Per-epoch checkpoints (weights, Adam moments, step): a resumed run continues bit for bit."""
+    from paper_1902_10559_gb300.warmstart import WarmStart
+    a = WarmStart(chunk=64, max_batch=32)
+    x, t = a.make_pairs(np.arange(128))
+    ck = tmp_path / "ws.npz"
+    a.train(x, t, epochs=1, batch=32, seed=1, checkpoint=str(ck))
+    b = WarmStart(chunk=64, max_batch=32)
+    b.load(str(ck))
+    assert b.steps == a.steps == 4
+    a.train(x, t, epochs=1, batch=32, seed=2)
+    b.train(x, t, epochs=1, batch=32, seed=2)
+    assert np.array_equal(a.cnn.params(), b.cnn.params())
