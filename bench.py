@@ -189,10 +189,6 @@ class Realistic:
     metric, unit, higher_is_better, dtype = METRIC, UNIT, True, "f32"
     two_process_baseline = True  # also time the oracle with A1 and A2 in two processes
 
-    def extra(self, ss):
-        """Workload-specific keys added to the JSON line."""
-        return {}
-
     def oracle_run(self, osart, case):
         """One oracle solve of a sampled case; returns the units it completed."""
         n, A1, A2, p1, p2 = case
@@ -242,6 +238,38 @@ class Realistic:
                           if self.tuned.get("kernel") == 2 else "sart_stream_kernel<TF32,LPC>",
                 "algorithmic_bytes_per_launch": alg, "peak_source": f"{kind} hbm_gbs",
                 "note": "per-iteration working set ~35 MB is L2/shared-memory resident within a solve"}
+
+    def extra(self, ss):
+        """Workload-specific keys added to the JSON line."""
+        return {"forms": self.form_times(ss, [self.geom])}
+
+    def form_times(self, ss, geoms):
+        """Solve time of the same inputs with BF16 and FP16 matrix values (per-row scales), beside FP32."""
+        import torch
+        out = {}
+        ts32 = None
+        for name, dt in (("f32", ss.F32), ("bf16", ss.BF16), ("f16", ss.F16)):
+            sysm = self.system if dt == ss.F32 else (
+                ss.fold_system(geoms[0], dt) if len(geoms) == 1 else ss.fold_batch(geoms, dt))
+            p12 = torch.empty(sysm.Mh, 2, device=self.p12.device)
+            ss.fold_rhs(sysm, self.p_in if hasattr(self, "p_in") else self.p, p12)
+            f12 = torch.zeros(sysm.Nh, 2, device=self.p12.device)
+            ts = []
+            for _ in range(3):
+                f12.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                ss.solve(sysm, p12, f12, self.opts)
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            out[name] = {"solve_ms": min(ts[1:]), "bytes_per_entry_per_pass": 12 if dt == ss.F32 else 8}
+            if dt != ss.F32:
+                out[name]["time_vs_f32"] = out[name]["solve_ms"] / out["f32"]["solve_ms"]
+                del sysm
+                torch.cuda.empty_cache()
+        out["note"] = "same inputs, launch shape and iterations as the timed FP32 solve"
+        return out
 
     def config(self):
         return {"workload": "realistic slice: 512x128 voxels, K=26 sources +/-25 deg, 1024 bins, 20 ellipses, "
@@ -332,6 +360,9 @@ class Batch(Realistic):
                 "algorithmic_bytes_per_launch": alg, "peak_source": f"{kind} hbm_gbs",
                 "note": "timed region = the replayed graph (fold of p, solve, recombine); inputs far exceed L2"}
 
+    def extra(self, ss):
+        return {"forms": self.form_times(ss, self.geoms)}
+
     def kernel_name(self):
         return {1: "sart_stream_kernel<TF32,LPC,batch> (CTA-wide staged tiles)",
                 2: "sart_resident_kernel<TF32,LPC>",
@@ -366,6 +397,9 @@ class Batch(Realistic):
 class Multi(Realistic):
     name = "multi"
     two_process_baseline = False
+
+    def extra(self, ss):
+        return {}
     config_id = 3
     profile = "sart_multi_tiny64_fp32.txt"
     NRHS = 64
