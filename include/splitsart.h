@@ -273,7 +273,8 @@ typedef struct splitsart_solve_opts {
     int32_t kernel;        /* 0 = choose (2 if the system fits on chip, else 3); 1 = stream the matrix in
                               CTA-wide tiles; 2 = keep it in shared memory; 3 = stream it row by row
                               through registers; 4 = stream it per warp through shared memory with
-                              bulk asynchronous copies. 3 and 4 have no CTA barriers inside a pass */
+                              bulk asynchronous copies (lanes_per_col 4 or 8 only). 3 and 4 have no
+                              CTA barriers inside a pass */
     double timeout_ms;     /* limit of each grid-barrier wait; 0 = default (2000 ms) */
     int32_t inject_barrier_fault; /* test hook: the barrier also waits for a CTA that never comes */
     int32_t tile_entries;  /* streaming kernel: entries staged per tile, 0 = default; multiple of 1024 in [1024, 16384] */

@@ -85,7 +85,7 @@ def solve_candidates(system: ss.System) -> list[dict]:
             for bt in (256, 384, 512):
                 out.append({"kernel": 2, "lanes_per_col": lpc, "block_threads": bt, "tile_entries": 0})
     for kern, bts in ((4, (256, 384)), (3, (256, 512))):
-        for lpc in (4, 8, 16):
+        for lpc in ((4, 8) if kern == 4 else (4, 8, 16)):
             for bt in bts:
                 out.append({"kernel": kern, "lanes_per_col": lpc, "block_threads": bt, "tile_entries": 0})
     for lpc in (4, 8, 16):

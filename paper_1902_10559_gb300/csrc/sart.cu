@@ -1788,7 +1788,12 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
         dyn = 0;
         block = threads > 512 ? 512 : threads;
     } else if (use_bulk) {
-        kern = batch ? (void*)sart_bulk_kernel<T, LPC, true> : (void*)sart_bulk_kernel<T, LPC, false>;
+        // Built for 4 and 8 lanes per column only (the shapes the autotuner tries).
+        if constexpr (LPC != 4 && LPC != 8) {
+            return fail(SPLITSART_ERR_ARG, "solve: kernel 4 supports lanes_per_col 4 or 8");
+        } else {
+            kern = batch ? (void*)sart_bulk_kernel<T, LPC, true> : (void*)sart_bulk_kernel<T, LPC, false>;
+        }
         block = threads > 384 ? 384 : threads;
         cudaFuncAttributes ba{};
         if ((e = cudaFuncGetAttributes(&ba, (const void*)kern)) != cudaSuccess) return cuda_fail(e, "solve: attributes");
