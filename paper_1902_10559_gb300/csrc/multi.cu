@@ -192,19 +192,22 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
         if (sub == 0) s_rr[wib][rw][g] = rr.sum();
         if (tid == 0) s_fin = 0u;
         __syncthreads();
-        // ---- stop tests, one thread per slot, fixed order ----
-        if (tid < RC && s_rhs[tid] >= 0) {
-            const int k = s_k[tid];
+        // ---- stop tests: one warp per slot sums its partials (lane-strided, fixed
+        // tree; FP64 is slow on this GPU, so no serial chain), and its lane 0 decides ----
+        for (int r = wib; r < RC; r += nwarps) {
+            if (s_rhs[r] < 0) continue;  // uniform over the warp
+            const int k = s_k[r];
             const bool last = k >= a.max_iters;
-            if (last || (k % a.check_every == 0)) {
-                double t0 = 0.0;
-                for (int w = 0; w < nwarps; ++w)
-                    for (int q = 0; q < RPW; ++q) t0 += s_rr[w][q][tid];
-                const double t1 = s_pp[tid];
+            if (!(last || (k % a.check_every == 0))) continue;
+            double t0 = 0.0;
+            for (int x = lane; x < nwarps * RPW; x += 32) t0 += s_rr[x / RPW][x % RPW][r];
+            t0 = warp_sum(t0);
+            if (lane == 0) {
+                const double t1 = s_pp[r];
                 const double rho = t1 > 0.0 ? sqrt(t0 / t1) : 0.0;
                 if (last || rho <= a.tol) {
-                    a.info[s_rhs[tid]] = splitsart_solve_info{k, SPLITSART_OK, rho, t0, t1};
-                    atomicOr(&s_fin, 1u << tid);
+                    a.info[s_rhs[r]] = splitsart_solve_info{k, SPLITSART_OK, rho, t0, t1};
+                    atomicOr(&s_fin, 1u << r);
                 }
             }
         }
