@@ -39,10 +39,14 @@ TARGET_ITERS = 500
 
 class WarmStart:
     def __init__(self, g=TINY, chunk: int = 1024, max_batch: int = 256, params=None, mode: int = 1,
-                 lam: float = 1.0):
+                 lam: float = 1.0, rhs_per_cta: int = 1):
         import torch
         self.g = g
         self.lam = lam
+        # One right-hand side per CTA: with more right-hand sides than resident slots,
+        # the persistent multi-RHS launch refills each slot as its right-hand side
+        # stops, so the time follows the mean iteration count, not the slowest one.
+        self.rhs_per_cta = rhs_per_cta
         self.geom = ss.make_geometry(g)
         self.system = ss.fold_system(self.geom, ss.F32)
         self.chunk = chunk
@@ -101,7 +105,7 @@ class WarmStart:
         import torch
         n = p12.shape[0]
         info = torch.zeros(n * ctypes.sizeof(ss.SolveInfo), dtype=torch.uint8, device=self.dev)
-        ss.solve_multi(self.system, p12, f12, ss.solve_opts(iters, self.lam, tol), info, rhs_per_cta=4)
+        ss.solve_multi(self.system, p12, f12, ss.solve_opts(iters, self.lam, tol), info, rhs_per_cta=self.rhs_per_cta)
         return info
 
     # ---- 1. data ----
