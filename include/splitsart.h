@@ -267,7 +267,9 @@ typedef struct splitsart_solve_opts {
     double lambda;         /* relaxation, 0 < lambda < 2 */
     double tol;            /* stop at the first k with rho_k <= tol; 0 = run max_iters */
     int32_t check_every;   /* test rho every this many iterations (>= 1; 0 means 1) */
-    int32_t block_threads; /* threads per CTA, 0 = library default (256) */
+    int32_t block_threads; /* threads per CTA, multiple of 32 in [64, 1024]; 0 = the kernel's default.
+                              Kernel 1: default 1024. Kernels 2 and 3: at most 512 (default 512;
+                              larger values run 512). Kernel 4: at most 384 (default 384) */
     int32_t ctas_per_sm;   /* 0 = as many as fit */
     int32_t lanes_per_col; /* back-projection lanes per column, 0 = default (8); 1,2,4,8,16,32 */
     int32_t kernel;        /* 0 = choose (2 if the system fits on chip, else 3); 1 = stream the matrix in
@@ -291,8 +293,13 @@ typedef struct splitsart_solve_opts {
  *     rho_k = sqrt(||r1^k||^2 + ||r2^k||^2) / sqrt(||p1||^2 + ||p2||^2),
  * which equals ||A f^k - p|| / ||p|| for the recombined image, the solve
  * returns f^k at the first tested k with rho_k <= tol, or at
- * k = max_iters. The update is skipped on the stopping pass. The norms are
- * accumulated in FP64 in a fixed order, so results are bitwise reproducible.
+ * k = max_iters. The update is skipped on the stopping pass. The squares of
+ * r are summed in FP32 groups of 16 and the group sums in FP64. With kernels
+ * 1 and 2 every sum has a fixed order, so repeated runs of one launch shape
+ * are bitwise identical (f^k and rho). Kernels 3 and 4 hand out rows
+ * dynamically: their per-row and per-column sums keep a fixed order, but the
+ * grouping of the norm sums does not, so rho can differ in its last bits from
+ * run to run.
  *
  * Arguments:
  * - p12_dev: pair[Mh] from splitsart_fold_rhs.

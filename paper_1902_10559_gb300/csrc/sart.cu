@@ -496,23 +496,26 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
 //
 // Each CTA copies its part of the folded matrix into shared memory once per
 // launch:
-// - a contiguous range of non-empty rows, and one of non-empty columns,
-//   balanced by their shared-memory bytes;
+// - its rows: a contiguous range of non-empty rows from the host's row plan
+//   (balanced by entries plus a fixed weight per row, since a row's fixed
+//   cost is of the order of its gathers), or, without a plan, a range
+//   balanced by shared-memory bytes;
+// - a contiguous range of non-empty columns, balanced by bytes;
 // - values, 16-bit indices, and the per-row/column metadata (p, 1/R, 1/C,
 //   its own f).
 // After that, an iteration's global traffic is only the gathers of f (forward)
 // and of u (back), the stores of u and f, and the norm partials.
 //
-// Inside a CTA each phase is split by entries, in the manner of a merge-based
-// CSR product. Thread t takes the entries [t k, (t+1) k) of the CTA's slice,
-// with k = ceil(entries / threads).
-// - It issues all of its gathers before it consumes any of them, so a phase
-//   costs about one memory round trip whatever the row lengths.
-// - It sums its run segment by segment (one segment per row or column).
-// - A row that spans threads is completed by the thread holding its last
-//   entry. That thread adds the earlier threads' carried tails in a fixed
-//   order.
-// Results are deterministic for a given launch shape.
+// Inside a CTA:
+// - forward: one warp per row, NR rows per warp in flight. Lane l takes the
+//   entries l, l + 32, ... of a row; each lane issues up to U gathers per row
+//   before it consumes any, then a shuffle tree sums the row.
+// - back: LPC lanes per column, two groups of columns per warp in flight,
+//   up to UB gathers per lane and column, then a shuffle tree over the group.
+// - The stop test of iteration k is decided by one thread per CTA while the
+//   first back-projection gathers are in flight.
+// The sums have a fixed order, so results are deterministic for a given
+// launch shape. The block is at most 512 threads (128 registers each).
 // ---------------------------------------------------------------------------
 
 // Shared-memory bytes per entry and per row/column of the resident layout.
@@ -1735,11 +1738,11 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
     if (rc) return rc;
 
     // Shared-memory residency: one CTA per SM, 16-bit indices.
-    auto rkern = sart_resident_kernel<T, LPC>;
+    void* rkern = (void*)sart_resident_kernel<T, LPC>;
+    const int res_threads = (o.block_threads > 0 && o.block_threads <= 512) ? o.block_threads : 512;
     cudaFuncAttributes fa{};
     e = cudaFuncGetAttributes(&fa, (const void*)rkern);
     if (e != cudaSuccess) return cuda_fail(e, "solve: kernel attributes");
-    const int res_threads = (o.block_threads > 0 && o.block_threads <= 512) ? o.block_threads : 512;
     const long long res_avail = (long long)smem_optin - (long long)fa.sharedSizeBytes -
                                 (long long)ResidentBytes<T>::kThread * res_threads - 32;
     const bool batch = s->ns > 1;
@@ -1778,7 +1781,7 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
     int block = threads;
     int te_bulk = 0;
     if (use_res) {
-        kern = (void*)rkern;
+        kern = rkern;
         dyn = (size_t)res_avail;
         smem_bytes = (int)dyn;
         grid = nsm;
