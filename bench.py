@@ -53,6 +53,7 @@ ITERS = 200
 LAMBDA = 0.8
 NOISE = 0.01
 KERNEL_SRC = os.path.join(ROOT, "paper_1902_10559_gb300", "csrc", "sart.cu")  # solve kernels
+MULTI_SRC = os.path.join(ROOT, "paper_1902_10559_gb300", "csrc", "multi.cu")  # multi-RHS solve kernel
 PROFILES = os.path.join(ROOT, "profiles")
 # Kernel launches of one device fold of A: count, scan (3), fill, row compaction (5),
 # CSC count, scan (3), place, sort + column sums, column compaction (5).
@@ -122,17 +123,17 @@ def read_peak(key: str, fallback: float):
         return fallback, "fallback"
 
 
-def profile_traffic(name: str):
+def profile_traffic(name: str, src: str = KERNEL_SRC):
     """Per-launch DRAM bytes of the solve kernel from a committed ncu summary.
 
-    Returns None if the summary is absent, or if the kernel source has changed
-    since it was taken.
+    Returns None if the summary is absent, or if the kernel's source file
+    (``src``) has changed since it was taken.
     """
     try:
         txt = open(os.path.join(PROFILES, name)).read()
     except OSError:
         return None
-    src_hash = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    src_hash = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
     m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     if not m_hash or not m_bytes or m_hash.group(1) != src_hash:
@@ -303,9 +304,15 @@ class Batch(Realistic):
         import torch
         from paper_1902_10559_gb300 import autotune
         from paper_1902_10559_gb300.synthetic import batch_geometries
+        from paper_1902_10559_gb300.synthetic import TINY
         self.gs = batch_geometries()[: self.n_slices]
-        self.geoms = [ss.make_geometry(g) for g in self.gs]
+        ss.make_geometries_device([TINY])  # loads the tracer's kernels
+        t0 = time.perf_counter()
+        self.geoms = ss.make_geometries_device(self.gs)
+        t1 = time.perf_counter()
         self.system = ss.fold_batch(self.geoms, ss.F32)
+        torch.cuda.synchronize()
+        self.geometry_s = {"device_tracer": t1 - t0, "device_tracer_and_fold": time.perf_counter() - t0}
         self.info = self.system.info()
         sysm = self.system
         self.p = phantoms_projections(ss, sysm, self.gs, dev, self.config_id, 12, rank, 0.0)
@@ -361,7 +368,19 @@ class Batch(Realistic):
                 "note": "timed region = the replayed graph (fold of p, solve, recombine); inputs far exceed L2"}
 
     def extra(self, ss):
-        return {"forms": self.form_times(ss, self.geoms)}
+        # Setup, outside the timed steps: the first-half rows of all slices
+        # traced on the GPU, and on the host cores for comparison.
+        import torch
+        t0 = time.perf_counter()
+        host = [ss.make_geometry(g) for g in self.gs]
+        t1 = time.perf_counter()
+        sysm = ss.fold_batch(host, ss.F32)
+        torch.cuda.synchronize()
+        self.geometry_s["host_tracer"] = t1 - t0
+        self.geometry_s["host_tracer_and_fold"] = time.perf_counter() - t0
+        self.geometry_s["host_threads"] = min(32, os.cpu_count() or 1)
+        del host, sysm
+        return {"forms": self.form_times(ss, self.geoms), "geometry_s": self.geometry_s}
 
     def kernel_name(self):
         return {1: "sart_stream_kernel<TF32,LPC,batch> (CTA-wide staged tiles)",
@@ -448,7 +467,7 @@ class Multi(Realistic):
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         ach = flops / (solve_ms / 1e3) / 1e12
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": profile_traffic(self.profile), "kernel": f"sart_multi_kernel<{self.ktype},RC>",
+                "traffic": profile_traffic(self.profile, MULTI_SRC), "kernel": f"sart_multi_kernel<{self.ktype},RC>",
                 "peak_source": "nominal FP32 FMA rate at 2.07 GHz",
                 "note": "system and vectors in shared memory; latency- and shared-memory-bound, not DRAM"}
 

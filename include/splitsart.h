@@ -100,6 +100,28 @@ typedef struct splitsart_system splitsart_system;     /* device: folded A1/A2, C
 int splitsart_make_geometry(const splitsart_geometry_params* params, splitsart_geometry** out);
 
 /*
+ * The same rows as splitsart_make_geometry, for n slices at once, traced on
+ * the GPU (one thread per ray; Section 2 geometry, Siddon lengths, FP64).
+ * - params[n]: one acquisition per slice. out[n] receives n geometries,
+ *   each bitwise equal to what splitsart_make_geometry returns for its
+ *   params (same rows, columns and FP64 lengths), owned by the caller (free
+ *   each with splitsart_geometry_destroy).
+ * - The columns and lengths stay in device memory (12 bytes per entry, one
+ *   allocation shared by the n geometries and freed with the last of them);
+ *   the row pointers are on the host. splitsart_fold_system/_fold_batch copy
+ *   the rows on the device; splitsart_geometry_export copies them to the
+ *   host.
+ * - stream: the CUDA stream of the device work (NULL: the default stream).
+ *   The call synchronises that stream before it returns.
+ * - Working memory while tracing: about 12 more bytes per entry and 16 per
+ *   ray, freed before the call returns.
+ * Errors: those of splitsart_make_geometry for any slice (then no geometry
+ * is returned); SPLITSART_ERR_CUDA or SPLITSART_ERR_NOMEM.
+ */
+int splitsart_make_geometries_device(const splitsart_geometry_params* params, int n, void* stream,
+                                     splitsart_geometry** out);
+
+/*
  * Wrap caller-supplied first-half rows of any matrix that satisfies Eq. (2).
  * For example, the 4 x 6 system of Example 1.
  * - row_ptr_host[Mh+1] (int64) and col_host/val_host[nnz] hold rows

@@ -5,7 +5,9 @@ parallel. Output: ``paper_1902_10559_gb300/libsplitsart.so``. Objects go to
 ``paper_1902_10559_gb300/_build/``.
 
 Host code is compiled with ``-ffp-contract=off``, so that the geometry
-(Siddon lengths) is bitwise identical on x86_64 and aarch64.
+(Siddon lengths) is bitwise identical on x86_64 and aarch64. The device
+tracer (``geometry_gpu.cu``) is compiled with ``-fmad=false`` for the same
+reason: it must give the host tracer's bits.
 """
 from __future__ import annotations
 
@@ -22,7 +24,9 @@ LIB = os.path.join(HERE, "libsplitsart.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["api.cu", "fold.cu", "sart.cu", "multi.cu", "cnn.cu", "cnn_mma.cu"]
+CU_SOURCES = ["api.cu", "fold.cu", "sart.cu", "multi.cu", "cnn.cu", "cnn_mma.cu", "geometry_gpu.cu"]
+# The device tracer must round like the host tracer: no fused multiply-adds.
+CU_FLAGS = {"geometry_gpu.cu": ["-fmad=false"]}
 CPP_SOURCES = ["geometry.cpp"]
 
 
@@ -58,7 +62,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         s = os.path.join(CSRC, src)
         o = os.path.join(BUILD, src + ".o")
         cmd = [nvcc, *ARCH, "-lineinfo", *common, "-Xcompiler", "-fPIC,-ffp-contract=off",
-               "--expt-relaxed-constexpr", "-c", s, "-o", o]
+               "--expt-relaxed-constexpr", *CU_FLAGS.get(src, []), "-c", s, "-o", o]
         jobs.append((o, s, cmd))
     for src in CPP_SOURCES:
         s = os.path.join(CSRC, src)

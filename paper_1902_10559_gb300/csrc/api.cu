@@ -276,12 +276,15 @@ int create_system(const splitsart_geometry* const* geoms, int ns, int dtype, cud
     hrp[Mh] = nnz;
     e = cudaMemcpyAsync(s->hrp, hrp.data(), sizeof(int64_t) * (Mh + 1), cudaMemcpyHostToDevice, st);
     for (int k = 0; k < ns && e == cudaSuccess; ++k) {
-        const HalfCsr& h = geoms[k]->half;
+        const splitsart_geometry* g = geoms[k];
         const int64_t n = nnzo[k + 1] - nnzo[k];
         if (n == 0) continue;
-        e = cudaMemcpyAsync(s->hcol + nnzo[k], h.col.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(s->hval + nnzo[k], h.val.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st);
+        // Rows traced on the device are copied there; host rows are uploaded.
+        const int32_t* col = g->dev ? g->dev->col + g->dev_off : g->half.col.data();
+        const double* val = g->dev ? g->dev->val + g->dev_off : g->half.val.data();
+        const cudaMemcpyKind kind = g->dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        e = cudaMemcpyAsync(s->hcol + nnzo[k], col, sizeof(int32_t) * n, kind, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s->hval + nnzo[k], val, sizeof(double) * n, kind, st);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->sl_rows, rows.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->sl_cols, cols.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, st);
@@ -289,7 +292,9 @@ int create_system(const splitsart_geometry* const* geoms, int ns, int dtype, cud
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->sl_N, No.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->sl_nx, nxs.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->sl_nz, nzs.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st);
-    // The host vectors above are pageable: the copies complete before cudaMemcpyAsync returns.
+    // The host vectors above are pageable: their copies complete before cudaMemcpyAsync
+    // returns. Device-traced rows are copied on the stream; cudaFree, which releases
+    // them with their geometries, waits for that copy.
     if (e != cudaSuccess) {
         splitsart_system_destroy(s);
         return cuda_fail(e, "fold: upload");

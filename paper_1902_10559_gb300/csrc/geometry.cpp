@@ -47,7 +47,9 @@ void trace(const Grid& g, double sx, double sz, double tx, double tz,
            std::vector<std::pair<int32_t, double>>& out, std::vector<double>& ax,
            std::vector<double>& az) {
     const double dx = tx - sx, dz = tz - sz;
-    const double L = std::hypot(dx, dz);
+    // A plain correctly rounded square root: the device tracer computes the
+    // same expression and gets the same bits.
+    const double L = std::sqrt(dx * dx + dz * dz);
     const double xlo = g.xplane(0), xhi = g.xplane(g.nx);
     const double zlo = g.zplane(0), zhi = g.zplane(g.nz);
 
@@ -129,7 +131,7 @@ void trace(const Grid& g, double sx, double sz, double tx, double tz,
 
 }  // namespace
 
-int build_half_rows(const splitsart_geometry_params& p, HalfCsr& h) {
+int make_acquisition(const splitsart_geometry_params& p, Acquisition& a) {
     if (p.nx <= 0 || p.nz <= 0 || p.K < 2 || p.nb <= 0 || !(p.W > 0) || !(p.H > 0) || !(p.R > 0) ||
         !(p.D > 0) || !(p.gamma_deg >= 0))
         return fail(SPLITSART_ERR_ARG, "make_geometry: sizes must be positive and K >= 2");
@@ -142,19 +144,31 @@ int build_half_rows(const splitsart_geometry_params& p, HalfCsr& h) {
                     (long long)M);
     const int64_t N = int64_t(p.nx) * p.nz;
     if (N > INT32_MAX) return fail(SPLITSART_ERR_ARG, "make_geometry: N too large for int32 column indices");
-
-    Grid g{p.nx, p.nz, p.W, p.H, p.z0, p.W / p.nx, p.H / p.nz};
+    a.M = M;
+    a.N = N;
+    a.Mh = M / 2;
     // Sources: source K-1-k is the exact mirror of source k.
-    std::vector<double> srcx(p.K), srcz(p.K);
+    a.srcx.assign(p.K, 0.0);
+    a.srcz.assign(p.K, 0.0);
     const double gam = p.gamma_deg * (M_PI / 180.0);
     for (int k = 0; 2 * k + 1 <= p.K; ++k) {
         const double th = gam * (2 * k + 1 - p.K) / (p.K - 1);
-        srcx[k] = p.R * std::sin(th);
-        srcz[k] = p.R * std::cos(th);
-        srcx[p.K - 1 - k] = -srcx[k];
-        srcz[p.K - 1 - k] = srcz[k];
+        a.srcx[k] = p.R * std::sin(th);
+        a.srcz[k] = p.R * std::cos(th);
+        a.srcx[p.K - 1 - k] = -a.srcx[k];
+        a.srcz[p.K - 1 - k] = a.srcz[k];
     }
-    const int64_t Mh = M / 2;
+    return SPLITSART_OK;
+}
+
+int build_half_rows(const splitsart_geometry_params& p, HalfCsr& h) {
+    Acquisition acq;
+    const int rc = make_acquisition(p, acq);
+    if (rc) return rc;
+    const int64_t M = acq.M, N = acq.N, Mh = acq.Mh;
+    const std::vector<double>& srcx = acq.srcx;
+    const std::vector<double>& srcz = acq.srcz;
+    Grid g{p.nx, p.nz, p.W, p.H, p.z0, p.W / p.nx, p.H / p.nz};
 
     unsigned nthr = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
     if (Mh < 4096) nthr = 1;
@@ -288,6 +302,7 @@ extern "C" int splitsart_geometry_info(const splitsart_geometry* g, int64_t* M, 
 extern "C" int splitsart_geometry_export(const splitsart_geometry* g, int64_t* rp, int32_t* col, double* val) {
     if (!g || !rp || !col || !val) return fail(SPLITSART_ERR_ARG, "geometry_export: NULL argument");
     std::memcpy(rp, g->half.row_ptr.data(), g->half.row_ptr.size() * sizeof(int64_t));
+    if (g->dev) return device_rows_to_host(DeviceRowsView{g->dev.get(), g->dev_off, g->half.row_ptr.back()}, col, val);
     std::memcpy(col, g->half.col.data(), g->half.col.size() * sizeof(int32_t));
     std::memcpy(val, g->half.val.data(), g->half.val.size() * sizeof(double));
     return SPLITSART_OK;

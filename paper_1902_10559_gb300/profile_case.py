@@ -3,7 +3,7 @@
 Usage:
     python -m paper_1902_10559_gb300.profile_case realistic [--iters N] [--kernel K] [--lpc L] [--threads T]
     python -m paper_1902_10559_gb300.profile_case batch --slices S [--iters N] [--kernel K] ...
-    python -m paper_1902_10559_gb300.profile_case multi [--nrhs R] [--iters N]
+    python -m paper_1902_10559_gb300.profile_case multi [--nrhs R] [--iters N] [--rc C] [--dtype f32|bf16|f16]
     python -m paper_1902_10559_gb300.profile_case cnn [--batch B]
 
 Each case builds its inputs, runs the kernel twice, and exits. The first run is
@@ -31,6 +31,8 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--nrhs", type=int, default=64)
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--rc", type=int, default=0, help="multi: right-hand sides per CTA (0 = library choice)")
+    ap.add_argument("--dtype", choices=["f32", "bf16", "f16"], default="f32", help="multi: matrix value storage")
     args = ap.parse_args()
     dev = torch.device("cuda")
 
@@ -59,7 +61,7 @@ def main():
         torch.cuda.synchronize()
         print("S", sysm.info()["S"], "result", ss.solve_result(sysm))
     elif args.case == "multi":
-        sysm = ss.fold_system(ss.make_geometry(TINY), ss.F32)
+        sysm = ss.fold_system(ss.make_geometry(TINY), ss.DTYPE_NAMES[args.dtype])
         vec = ss.fold_batch([ss.make_geometry(TINY)] * args.nrhs, ss.F32)
         p = torch.empty(vec.M, device=dev)
         ss.project(vec, phantoms([TINY] * args.nrhs, 3, 8), p, layout=ss.LAYOUT_IMAGE)
@@ -69,7 +71,8 @@ def main():
         info = torch.zeros(args.nrhs * ctypes.sizeof(ss.SolveInfo), dtype=torch.uint8, device=dev)
         for _ in range(2):
             f12.zero_()
-            ss.solve_multi(sysm, p12, f12, ss.solve_opts(args.iters, 0.8, block_threads=args.threads), info)
+            ss.solve_multi(sysm, p12, f12, ss.solve_opts(args.iters, 0.8, block_threads=args.threads), info,
+                           rhs_per_cta=args.rc)
         torch.cuda.synchronize()
         print("multi", ss.read_infos(info, 1)[0])
     else:

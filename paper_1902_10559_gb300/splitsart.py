@@ -65,6 +65,8 @@ _P = ctypes.c_void_p
 _SIGS = {
     "splitsart_make_geometry": ([ctypes.POINTER(GeometryParams), ctypes.POINTER(_P)], ctypes.c_int),
     "splitsart_make_geometry_from_csr": ([ctypes.c_int64, ctypes.c_int64, _P, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "splitsart_make_geometries_device": ([ctypes.POINTER(GeometryParams), ctypes.c_int, _P, ctypes.POINTER(_P)],
+                                         ctypes.c_int),
     "splitsart_geometry_info": ([_P, _P, _P, _P], ctypes.c_int),
     "splitsart_geometry_export": ([_P, _P, _P, _P], ctypes.c_int),
     "splitsart_geometry_destroy": ([_P], None),
@@ -184,6 +186,16 @@ def make_geometry(g) -> Geometry:
     h = ctypes.c_void_p()
     _check(lib().splitsart_make_geometry(ctypes.byref(p), ctypes.byref(h)))
     return Geometry(h.value, g)
+
+
+def make_geometries_device(gs, stream=None) -> list:
+    """Trace the geometries of several slices on the GPU (same rows as ``make_geometry``, bit for bit)."""
+    gs = list(gs)
+    params = (GeometryParams * len(gs))(*[GeometryParams(g.nx, g.nz, g.W, g.H, g.z0, g.K, g.gamma_deg, g.R, g.nb, g.D)
+                                          for g in gs])
+    out = (_P * len(gs))()
+    _check(lib().splitsart_make_geometries_device(params, len(gs), _stream_ptr(stream), out))
+    return [Geometry(out[k], g) for k, g in enumerate(gs)]
 
 
 def make_geometry_from_csr(M: int, N: int, row_ptr, col, val) -> Geometry:
