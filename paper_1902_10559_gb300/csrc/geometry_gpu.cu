@@ -78,35 +78,47 @@ __device__ void trace_ray(const SliceGeo& g, double sx, double sz, double tx, do
     if (!(amax > amin)) return;
 
     // Crossings strictly inside (amin, amax), in increasing a: the planes in
-    // ascending order, or descending when the direction is negative.
-    int cx = dx < 0.0 ? g.nx : 0, nx_left = dx != 0.0 ? g.nx + 1 : 0;
-    const int stx = dx < 0.0 ? -1 : 1;
-    int rz = dz < 0.0 ? g.nz : 0, nz_left = g.nz + 1;
-    const int stz = dz < 0.0 ? -1 : 1;
+    // ascending order, or descending when the direction is negative. The host
+    // tests every plane. Here a is the same expression, and it is monotone
+    // along that order (each step of it rounds monotonically), so the planes
+    // with a > amin are a suffix, found by bisection, and those with a < amax
+    // a prefix: the walk starts at the suffix and ends at the first a >= amax.
+    // The crossings are the host's, in the host's order, with fewer divisions.
+    const int stx = dx < 0.0 ? -1 : 1, stz = dz < 0.0 ? -1 : 1;
+    const int cx0 = dx < 0.0 ? g.nx : 0, rz0 = dz < 0.0 ? g.nz : 0;
+    auto a_x = [&](int q) { return (xplane(g, cx0 + stx * q) - sx) / dx; };
+    auto a_z = [&](int q) { return (zplane(g, rz0 + stz * q) - sz) / dz; };
+    auto first_above = [&](auto&& a_of, int n) {  // first q in [0, n) with a_of(q) > amin, or n
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (a_of(mid) > amin) hi = mid;
+            else lo = mid + 1;
+        }
+        return lo;
+    };
+    const int nqx = dx != 0.0 ? g.nx + 1 : 0, nqz = g.nz + 1;
+    int qx = first_above(a_x, nqx), qz = first_above(a_z, nqz);
     double ax = 0.0, az = 0.0;
     auto next_x = [&]() {
-        while (nx_left > 0) {
-            const double a = (xplane(g, cx) - sx) / dx;
-            cx += stx;
-            --nx_left;
-            if (a > amin && a < amax) {
-                ax = a;
-                return true;
-            }
+        if (qx >= nqx) return false;
+        const double a = a_x(qx++);
+        if (!(a < amax)) {
+            qx = nqx;
+            return false;
         }
-        return false;
+        ax = a;
+        return true;
     };
     auto next_z = [&]() {
-        while (nz_left > 0) {
-            const double a = (zplane(g, rz) - sz) / dz;
-            rz += stz;
-            --nz_left;
-            if (a > amin && a < amax) {
-                az = a;
-                return true;
-            }
+        if (qz >= nqz) return false;
+        const double a = a_z(qz++);
+        if (!(a < amax)) {
+            qz = nqz;
+            return false;
         }
-        return false;
+        az = a;
+        return true;
     };
 
     // A vertical ray on a boundary plane gives half its length to each side.

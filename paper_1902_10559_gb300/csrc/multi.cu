@@ -7,9 +7,12 @@
 //
 // Layout. The whole folded system (CSR, CSC, normalisers) is copied into each
 // CTA's shared memory once per launch. Each CTA has RC slots, each holding one
-// right-hand side's p, u and f, also in shared memory. An iteration therefore
-// touches no global memory, and the two phases are separated by CTA barriers
-// only. The launch needs no grid-wide synchronisation.
+// right-hand side's p, u and two buffers of f (f^k read, f^{k+1} written),
+// also in shared memory. An iteration therefore touches no global memory, and
+// its two phases are separated by two CTA barriers. The stop test of pass k
+// runs on one warp per slot while the other warps back-project; a slot that
+// stops returns f^k from the buffer the pass did not write. The launch needs
+// no grid-wide synchronisation.
 //
 // Scheduling. The launch is persistent: as many CTAs as are resident at once.
 // When a slot's right-hand side stops, its f and stop record are written out
@@ -68,7 +71,6 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
     __shared__ double s_pp[RC];
     __shared__ int s_rhs[RC];    // right-hand side held by each slot, or -1
     __shared__ int s_k[RC];      // iterations done by the slot's right-hand side
-    __shared__ int s_fresh[RC];  // refilled in this pass: no update until its first forward pass
     __shared__ unsigned s_fin;   // slots whose right-hand side stopped in this pass
     __shared__ int s_active;
 
@@ -101,7 +103,9 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
     off = align16m(off + sizeof(V2) * (size_t)Mh * RC);
     V2* s_u = reinterpret_cast<V2*>(smem + off);  // [Mh][RC]
     off = align16m(off + sizeof(V2) * (size_t)Mh * RC);
-    V2* s_f = reinterpret_cast<V2*>(smem + off);  // [Nh][RC]
+    V2* s_f = reinterpret_cast<V2*>(smem + off);  // [Nh][RC]: f^k, read by this pass
+    off = align16m(off + sizeof(V2) * (size_t)Nh * RC);
+    V2* s_fn = reinterpret_cast<V2*>(smem + off);  // [Nh][RC]: f^{k+1}, written by this pass
 
     for (int i = tid; i <= Mh; i += blockDim.x) s_rp[i] = a.rp[i];
     for (int j = tid; j <= Nh; j += blockDim.x) s_cp[j] = a.cp[j];
@@ -117,14 +121,14 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
     }
     for (int j = tid; j < Nh; j += blockDim.x) s_ic[j] = a.invC[j];
     // ---- slots: load, store, and ||p||^2 of newly loaded right-hand sides ----
-    auto load_slots = [&](unsigned mask) {
+    auto load_slots = [&](unsigned mask, V2* fdst) {
         for (int t = tid; t < Mh * RC; t += blockDim.x) {
             const int i = t / RC, r = t % RC;
             if (mask >> r & 1u) s_p[t] = s_rhs[r] >= 0 ? a.p12[(size_t)s_rhs[r] * Mh + i] : V2{};
         }
         for (int t = tid; t < Nh * RC; t += blockDim.x) {
             const int j = t / RC, r = t % RC;
-            if (mask >> r & 1u) s_f[t] = s_rhs[r] >= 0 ? a.f12[(size_t)s_rhs[r] * Nh + j] : V2{};
+            if (mask >> r & 1u) fdst[t] = s_rhs[r] >= 0 ? a.f12[(size_t)s_rhs[r] * Nh + j] : V2{};
         }
         __syncthreads();
         // ||p||^2 once per right-hand side: one warp per slot, lane-strided, fixed tree.
@@ -151,10 +155,9 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
         const int r = blockIdx.x * RC + tid;
         s_rhs[tid] = r < a.nrhs ? r : -1;
         s_k[tid] = 0;
-        s_fresh[tid] = 0;
     }
     __syncthreads();
-    load_slots((1u << RC) - 1u);
+    load_slots((1u << RC) - 1u, s_f);
     __syncthreads();
 
     for (;;) {
@@ -192,8 +195,11 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
         if (sub == 0) s_rr[wib][rw][g] = rr.sum();
         if (tid == 0) s_fin = 0u;
         __syncthreads();
-        // ---- stop tests: one warp per slot sums its partials (lane-strided, fixed
-        // tree; FP64 is slow on this GPU, so no serial chain), and its lane 0 decides ----
+        // ---- stop tests, overlapped with the back-projection ----
+        // One warp per slot sums its partials (lane-strided, fixed tree; FP64 is
+        // slow on this GPU, so no serial chain) and its lane 0 decides. The other
+        // warps start the back-projection meanwhile: it writes f^{k+1} into the
+        // second buffer, so a slot that stops still holds f^k in the first.
         for (int r = wib; r < RC; r += nwarps) {
             if (s_rhs[r] < 0) continue;  // uniform over the warp
             const int k = s_k[r];
@@ -211,31 +217,6 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
                 }
             }
         }
-        __syncthreads();
-        const unsigned fin = s_fin;
-        if (fin) {
-            // Return the stopped right-hand sides' f and refill their slots from the queue.
-            store_slots(fin);
-            __syncthreads();
-            if (tid == 0) {
-                int active = 0;
-                for (int r = 0; r < RC; ++r) {
-                    if (fin >> r & 1u) {
-                        const int nxt = (int)atomicAdd(a.queue, 1u) + (int)gridDim.x * RC;
-                        s_rhs[r] = nxt < a.nrhs ? nxt : -1;
-                        s_k[r] = 0;
-                        s_fresh[r] = 1;
-                    }
-                    active += s_rhs[r] >= 0;
-                }
-                s_active = active;
-            }
-            __syncthreads();
-            if (s_active == 0) break;
-            load_slots(fin);
-            __syncthreads();
-        }
-        // ---- back-projection and update for the slots still running ----
         for (int j0 = wib * RPW; j0 < Nh; j0 += nwarps * RPW) {
             const int j = j0 + rw;
             Acc b1 = 0, b2 = 0;
@@ -251,20 +232,43 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
             }
             b1 = warp_sum(b1, LPR);
             b2 = warp_sum(b2, LPR);
-            if (sub == 0 && j < Nh && s_rhs[g] >= 0 && !s_fresh[g]) {
+            if (sub == 0 && j < Nh) {
                 const N2 ic = s_ic[j];
                 V2 f = s_f[j * RC + g];
                 f.x += lam * b1 * ic.x;
                 f.y += lam * b2 * ic.y;
-                s_f[j * RC + g] = f;
+                s_fn[j * RC + g] = f;
             }
         }
         __syncthreads();
-        if (tid < RC) {
-            if (s_rhs[tid] >= 0 && !s_fresh[tid]) ++s_k[tid];
-            s_fresh[tid] = 0;
+        const unsigned fin = s_fin;  // read by every thread before any later write of s_fin
+        if (tid < RC && s_rhs[tid] >= 0) ++s_k[tid];
+        if (fin) {
+            // Return the stopped right-hand sides' f^k and refill their slots from
+            // the queue; a new right-hand side's f0 goes into the buffer that the
+            // next pass reads.
+            store_slots(fin);
+            __syncthreads();
+            if (tid == 0) {
+                int active = 0;
+                for (int r = 0; r < RC; ++r) {
+                    if (fin >> r & 1u) {
+                        const int nxt = (int)atomicAdd(a.queue, 1u) + (int)gridDim.x * RC;
+                        s_rhs[r] = nxt < a.nrhs ? nxt : -1;
+                        s_k[r] = 0;
+                    }
+                    active += s_rhs[r] >= 0;
+                }
+                s_active = active;
+            }
+            __syncthreads();
+            if (s_active == 0) break;
+            load_slots(fin, s_fn);
+            __syncthreads();
         }
-        __syncthreads();
+        V2* const t = s_f;
+        s_f = s_fn;
+        s_fn = t;
     }
 }
 
@@ -274,7 +278,7 @@ size_t multi_smem_bytes(const splitsart_system* s, int S, int RC) {
     const size_t pb = sizeof(typename T::Pair), nb = sizeof(typename T::KNorm2), vb = sizeof(typename T::Vec2);
     return al(4 * (s->Mh + 1)) + al(4 * (size_t)S) + al(pb * S) + al(4 * (s->Nh + 1)) + al(4 * (size_t)S) +
            al(pb * S) + al(nb * s->Mh) + al(nb * s->Nh) + (T::kQuant ? al(8 * s->Mh) : 0) + 2 * al(vb * s->Mh * RC) +
-           al(vb * s->Nh * RC);
+           2 * al(vb * s->Nh * RC);
 }
 
 template <class T, int RC>

@@ -77,3 +77,33 @@ def test_multi_rhs_stop_individually(ss, case):
     assert len(set(expect)) > 1
     infos, f12 = run(ss, system, ps[:8], 80, 1.0, tol=tol, rc=4)
     assert [i["iters"] for i in infos] == expect
+
+
+def test_multi_rhs_queue_refills_slots(ss):
+    """More right-hand sides than resident slots: stopped slots are refilled from the queue.
+
+    Every right-hand side still stops at the oracle's iteration and returns the oracle's f.
+    """
+    g = TINY
+    A = ogeo.mirrored_system_matrix(g)
+    A1, A2 = osplit.fold_matrix(A)
+    n = 700
+    ps = [A @ ogeo.image_to_snake(g, random_phantom(g, 41, 8, stream=r)) for r in range(n)]
+    system = ss.fold_system(ss.make_geometry(g), ss.F64)
+    sample = [0, 1, 151, 152, 303, 304, 455, 699]
+    hists = {}
+    for r in sample:
+        p1, p2 = osplit.fold_rhs(ps[r])
+        hists[r] = osart.split_sart(A1, A2, p1, p2, 1.0, 120, record=True)["rho_hist"]
+    tol = float(np.median([h[40] for h in hists.values()]))
+    infos, f12 = run(ss, system, ps, 120, 1.0, tol=tol, rc=1)
+    assert all(i["status"] == 0 for i in infos)
+    iters = [i["iters"] for i in infos]
+    assert len(set(iters)) > 1
+    for r in sample:
+        p1, p2 = osplit.fold_rhs(ps[r])
+        ref = osart.split_sart(A1, A2, p1, p2, 1.0, 120, tol=tol)
+        assert iters[r] == ref["iters"], r
+        f = osplit.recombine(f12[r, :, 0], f12[r, :, 1])
+        f_ref = osplit.recombine(ref["f1"], ref["f2"])
+        assert np.linalg.norm(f - f_ref) <= 1e-10 * np.linalg.norm(f_ref), r
