@@ -302,6 +302,9 @@ typedef struct splitsart_solve_opts {
     double timeout_ms;     /* limit of each grid-barrier wait; 0 = default (2000 ms) */
     int32_t inject_barrier_fault; /* test hook: the barrier also waits for a CTA that never comes */
     int32_t tile_entries;  /* streaming kernel: entries staged per tile, 0 = default; multiple of 1024 in [1024, 16384] */
+    int32_t row_weight;    /* kernel 2: when rows are dealt to CTAs, each row weighs this many entries more than
+                              its length (a row's fixed cost). 0 = default: the heaviest of 240, 160, 80, 40, 0
+                              whose plan fits in shared memory; a value that does not fit falls back the same way */
 } splitsart_solve_opts;
 
 /*

@@ -83,7 +83,9 @@ def solve_candidates(system: ss.System) -> list[dict]:
     if system.nslices == 1:
         for lpc in (4, 8, 16):
             for bt in (256, 384, 512):
-                out.append({"kernel": 2, "lanes_per_col": lpc, "block_threads": bt, "tile_entries": 0})
+                for rw in (0, 160, 320):  # rows' fixed weight in the CTA row plan (0 = library default)
+                    out.append({"kernel": 2, "lanes_per_col": lpc, "block_threads": bt, "tile_entries": 0,
+                                "row_weight": rw})
     for kern, bts in ((4, (256, 384)), (3, (256, 512))):
         for lpc in ((4, 8) if kern == 4 else (4, 8, 16)):
             for bt in bts:

@@ -52,6 +52,7 @@ struct MultiArgs {
     int Mh, Nh, S, nrhs;
     int max_iters, check_every;
     double lambda, tol;
+    double tol2_hi;  // tol^2 (1 + 1e-12): rr > pp tol2_hi proves rho > tol without a division or square root
 };
 
 __device__ __forceinline__ size_t align16m(size_t x) { return (x + 15) & ~size_t(15); }
@@ -210,8 +211,10 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
             t0 = warp_sum(t0);
             if (lane == 0) {
                 const double t1 = s_pp[r];
-                const double rho = t1 > 0.0 ? sqrt(t0 / t1) : 0.0;
-                if (last || rho <= a.tol) {
+                // The common case (rho > tol for certain) needs no FP64 division or square root.
+                const bool above = !last && t1 > 0.0 && t0 > t1 * a.tol2_hi;
+                const double rho = (above || !(t1 > 0.0)) ? 0.0 : sqrt(t0 / t1);
+                if (!above && (last || rho <= a.tol)) {
                     a.info[s_rhs[r]] = splitsart_solve_info{k, SPLITSART_OK, rho, t0, t1};
                     atomicOr(&s_fin, 1u << r);
                 }
@@ -323,6 +326,7 @@ int launch_multi(splitsart_system* s, int S, int nrhs, const void* p12, void* f1
     a.check_every = o.check_every > 0 ? o.check_every : 1;
     a.lambda = o.lambda;
     a.tol = o.tol;
+    a.tol2_hi = o.tol * o.tol * (1.0 + 1e-12);
     const int threads = o.block_threads > 0 ? o.block_threads : 512;
     if (threads % 32 || threads > 512 || threads < 32)
         return fail(SPLITSART_ERR_ARG, "solve_multi: block_threads must be a multiple of 32 in [32, 512]");

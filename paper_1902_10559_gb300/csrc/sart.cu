@@ -74,6 +74,7 @@ struct SartArgs {
     const FoldStats* stats;
     int max_iters, check_every;
     double lambda, tol;
+    double tol2_hi;  // tol^2 (1 + 1e-12): rr > pp tol2_hi proves rho > tol without a division or square root
     unsigned long long timeout_ns;
     unsigned expected;  // CTAs the barrier waits for
     int tile_entries;   // TE
@@ -110,8 +111,9 @@ __device__ void slice_stop_tests(const A& a, int k, bool last, double* red) {
             const double trr = warp_sum(lane < nwarps ? red[lane] : 0.0);
             if (lane == 0) {
                 const double tpp = __ldcg(&a.sl_solve[sl].pp);
-                const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
-                if (last || rho <= a.tol) {
+                const bool above = !last && tpp > 0.0 && trr > tpp * a.tol2_hi;  // rho > tol for certain
+                const double rho = (above || !(tpp > 0.0)) ? 0.0 : sqrt(trr / tpp);
+                if (!above && (last || rho <= a.tol)) {
                     a.sl_solve[sl] = SliceSolve{k, 1, rho, trr, tpp};
                     atomicAdd(a.ndone, 1);
                 }
@@ -123,8 +125,12 @@ __device__ void slice_stop_tests(const A& a, int k, bool last, double* red) {
 
 // The joint stop test (one thread): rho = sqrt(rr / pp), 0 when pp = 0. CTA 0
 // records the result of the stopping pass. Returns 1 to stop.
+// rr > pp tol^2 (1 + 1e-12) proves rho > tol whatever the rounding of the
+// division and the square root (a few ulps), so the common case skips both:
+// FP64 division and square root are long dependent chains on this GPU.
 template <class A>
 __device__ __forceinline__ int stop_test(const A& a, int k, bool last, double trr, double tpp) {
+    if (!last && tpp > 0.0 && trr > tpp * a.tol2_hi) return 0;
     const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
     const bool stop = last || rho <= a.tol;
     if (stop && blockIdx.x == 0) {
@@ -1620,6 +1626,7 @@ void fill_args(SartArgs<T>& a, splitsart_system* s, const void* p12, void* f12, 
     a.check_every = o.check_every > 0 ? o.check_every : 1;
     a.lambda = o.lambda;
     a.tol = o.tol;
+    a.tol2_hi = o.tol * o.tol * (1.0 + 1e-12);
     const double tms = o.timeout_ms > 0 ? o.timeout_ms : 2000.0;
     a.timeout_ns = (unsigned long long)(tms * 1e6);
     a.expected = grid + (o.inject_barrier_fault ? 1u : 0u);
@@ -1644,7 +1651,8 @@ void fill_args(SartArgs<T>& a, splitsart_system* s, const void* p12, void* f12, 
 // realistic slice a byte-balanced split gave CTAs from 29 to 134 rows and
 // forward passes from 2.8 to 6.6 us, with every CTA then waiting for the
 // slowest at the grid barrier. Here each row weighs row_weight entries more
-// than its length. Ranges keep the rows' order, so neighbouring rays (which
+// than its length (default 240: on the realistic slice 200 iterations took
+// 2.62 ms with weight 0, 2.37 ms with 160, 2.33 ms with 240, 2.67 ms with 480). Ranges keep the rows' order, so neighbouring rays (which
 // gather neighbouring voxels) stay together. Built on the first resident solve
 // and kept: the rows do not change across refolds.
 template <class T>
@@ -1733,6 +1741,8 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
     const int threads = o.block_threads > 0 ? o.block_threads : 1024;
     if (threads % 32 != 0 || threads > 1024 || threads < 64)
         return fail(SPLITSART_ERR_ARG, "solve: block_threads must be a multiple of 32 in [64, 1024]");
+    if (o.row_weight < 0 || o.row_weight > 100000)
+        return fail(SPLITSART_ERR_ARG, "solve: row_weight must be in [0, 100000]");
     FoldStats fs;
     int rc = system_host_stats(s, &fs);
     if (rc) return rc;
@@ -1750,11 +1760,14 @@ int launch_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_
     long long need = resident_bound<T>(fs, nsm);
     bool use_plan = false;
     if (res_shape && (o.kernel == 0 || o.kernel == 2)) {
-        // Heaviest row weight whose plan fits in shared memory (weight 0 balances entries alone).
+        // The asked row weight, else the heaviest default whose plan fits in
+        // shared memory (weight 0 balances entries alone).
         using B = ResidentBytes<T>;
         const long long Wc = (long long)B::kEntry * fs.S + (long long)B::kCol * fs.n_nzc;
         const long long col_part = (Wc + nsm - 1) / nsm + (long long)B::kEntry * fs.max_col + B::kCol + B::kSlack;
-        for (int w : {160, 80, 40, 0}) {
+        const int asked = o.row_weight > 0 ? o.row_weight : 240;
+        for (int w : {asked, 240, 160, 80, 40, 0}) {
+            if (w > asked) continue;
             rc = resident_plan<T>(s, fs, nsm, w, st);
             if (rc) return rc;
             if (s->res_row_bytes + col_part <= res_avail) {
@@ -1992,6 +2005,7 @@ int launch_static(StaticScratch* sc, int Mh, int Nh, const int32_t* rp, const in
     a.check_every = o.check_every > 0 ? o.check_every : 1;
     a.lambda = o.lambda;
     a.tol = o.tol;
+    a.tol2_hi = o.tol * o.tol * (1.0 + 1e-12);
     const double tms = o.timeout_ms > 0 ? o.timeout_ms : 2000.0;
     a.timeout_ns = (unsigned long long)(tms * 1e6);
     a.expected = (unsigned)grid + (o.inject_barrier_fault ? 1u : 0u);

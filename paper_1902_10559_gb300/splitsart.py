@@ -44,7 +44,8 @@ class SolveOpts(ctypes.Structure):
                 ("check_every", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("lanes_per_col", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("timeout_ms", ctypes.c_double),
-                ("inject_barrier_fault", ctypes.c_int32), ("tile_entries", ctypes.c_int32)]
+                ("inject_barrier_fault", ctypes.c_int32), ("tile_entries", ctypes.c_int32),
+                ("row_weight", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -326,11 +327,12 @@ def project(system: System, f, p, layout: int = LAYOUT_SNAKE, stream=None) -> No
 
 def solve_opts(max_iters: int, lam: float, tol: float = 0.0, check_every: int = 1, block_threads: int = 0,
                ctas_per_sm: int = 0, lanes_per_col: int = 0, timeout_ms: float = 0.0,
-               inject_barrier_fault: bool = False, kernel: int = 0, tile_entries: int = 0) -> SolveOpts:
+               inject_barrier_fault: bool = False, kernel: int = 0, tile_entries: int = 0,
+               row_weight: int = 0) -> SolveOpts:
     """Solve options (splitsart_solve_opts). kernel: 0 = library choice, 1 = CTA-wide tiles,
     2 = shared-memory resident, 3 = row streaming, 4 = per-warp bulk copies."""
     return SolveOpts(max_iters, lam, tol, check_every, block_threads, ctas_per_sm, lanes_per_col, kernel, timeout_ms,
-                     int(inject_barrier_fault), tile_entries)
+                     int(inject_barrier_fault), tile_entries, row_weight)
 
 
 def solve(system: System, p12, f12, opts: SolveOpts, stream=None) -> None:
