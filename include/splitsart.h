@@ -404,6 +404,7 @@ int splitsart_solve_static(int64_t Mh, int64_t Nh, const int32_t* rp_dev, const 
  *   4, 8, 16). Every matrix entry read serves all of them.
  * - An iteration touches no global memory, so the launch needs no grid-wide
  *   barrier.
+ * - opts->block_threads: a multiple of 32 in [32, 1024] (0 = 512).
  * - The system must be a single slice small enough for shared memory.
  *   Otherwise SPLITSART_ERR_ARG: use splitsart_solve per right-hand side.
  * Arguments:

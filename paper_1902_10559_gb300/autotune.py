@@ -140,7 +140,7 @@ def tune_multi(system: ss.System, p12, f12, iters: int = 10, use_cache: bool = T
         best, best_t = None, float("inf")
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for rc in (1, 2, 4, 8, 16):
-            for bt in (128, 256, 512):
+            for bt in (128, 256, 512, 1024):
                 try:
                     ts = []
                     for r in range(3):

@@ -60,7 +60,7 @@ __device__ __forceinline__ size_t align16m(size_t x) { return (x + 15) & ~size_t
 // RC right-hand sides per CTA; RPW rows (or columns) per warp at a time; the
 // 32 lanes split into RPW x RC groups of LPR = 32 / (RPW RC) lanes.
 template <class T, int RC, int RPW>
-__global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
+__global__ void __launch_bounds__(1024, 1) sart_multi_kernel(MultiArgs<T> a) {
     using Acc = typename T::Acc;
     using V2 = typename T::Vec2;
     using N2 = typename T::KNorm2;
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(512) sart_multi_kernel(MultiArgs<T> a) {
     constexpr int LPR = 32 / (RC * RPW);  // lanes per (row, right-hand side)
     static_assert(LPR >= 1, "too many groups per warp");
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double s_rr[16][RPW][RC];
+    __shared__ double s_rr[32][RPW][RC];  // per warp (at most 32) and lane group
     __shared__ double s_pp[RC];
     __shared__ int s_rhs[RC];    // right-hand side held by each slot, or -1
     __shared__ int s_k[RC];      // iterations done by the slot's right-hand side
@@ -328,8 +328,8 @@ int launch_multi(splitsart_system* s, int S, int nrhs, const void* p12, void* f1
     a.tol = o.tol;
     a.tol2_hi = o.tol * o.tol * (1.0 + 1e-12);
     const int threads = o.block_threads > 0 ? o.block_threads : 512;
-    if (threads % 32 || threads > 512 || threads < 32)
-        return fail(SPLITSART_ERR_ARG, "solve_multi: block_threads must be a multiple of 32 in [32, 512]");
+    if (threads % 32 || threads > 1024 || threads < 32)
+        return fail(SPLITSART_ERR_ARG, "solve_multi: block_threads must be a multiple of 32 in [32, 1024]");
     // Persistent: as many CTAs as are resident at once; a CTA refills a slot from
     // the queue as soon as its right-hand side stops.
     int nsm = 0, per_sm = 0;
