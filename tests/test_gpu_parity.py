@@ -270,7 +270,7 @@ def test_bad_solve_arguments(ss, tiny):
     p12 = torch.zeros(sysm.Mh, 2, device=DEV)
     f12 = torch.zeros(sysm.Nh, 2, device=DEV)
     for kw in ({"lam": 0.0}, {"lam": 1.0, "tol": -1.0}, {"lam": 1.0, "lanes_per_col": 3},
-               {"lam": 1.0, "block_threads": 48}):
+               {"lam": 1.0, "block_threads": 48}, {"lam": 1.0, "row_weight": -1}):
         lam = kw.pop("lam")
         with pytest.raises(ss.SplitSartError) as e:
             ss.solve(sysm, p12, f12, ss.solve_opts(5, lam, **kw))
@@ -309,6 +309,17 @@ def test_resident_and_streaming_kernels_agree_with_oracle(ss, tiny, dt, tol):
         assert info["iters"] == 60
         assert rel(f, f_ref) <= tol, (kernel, rel(f, f_ref))
         assert abs(info["rho"] - ref["rho"]) <= tol * ref["rho"]
+
+
+@pytest.mark.parametrize("dt", ["f32", "bf16"])
+def test_resident_row_plans_give_the_same_f(ss, realistic, dt):
+    """The row weight only changes which CTA holds a row; each row's sum keeps its order, so f is bitwise equal."""
+    c = realistic
+    sysm = ss.fold_system(ss.make_geometry(c.g), ss.DTYPE_NAMES[dt])
+    runs = [run_solve(ss, sysm, c.p, 40, 0.8, kernel=2, lanes_per_col=4, row_weight=w) for w in (1, 160, 320)]
+    for info, f12, _ in runs[1:]:
+        assert info["iters"] == 40 and np.array_equal(f12, runs[0][1])
+        assert abs(info["rho"] - runs[0][0]["rho"]) <= 1e-6 * runs[0][0]["rho"]  # norm groups follow the plan
 
 
 @pytest.mark.slow
