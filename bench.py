@@ -185,6 +185,7 @@ class Realistic:
     name = "realistic"
     config_id = 2
     profile = "sart_resident_realistic_fp32.txt"
+    default_steps = 100  # about 0.26 s of timed steps
     iters = ITERS
     lam = LAMBDA
     metric, unit, higher_is_better, dtype = METRIC, UNIT, True, "f32"
@@ -298,6 +299,7 @@ class Batch(Realistic):
     two_process_baseline = False
     config_id = 3
     profile = "sart_rows_batch256_fp32.txt"
+    default_steps = 10
     n_slices = 256
 
     def setup(self, ss, dev, rank):
@@ -421,6 +423,7 @@ class Multi(Realistic):
         return {}
     config_id = 3
     profile = "sart_multi_tiny64_fp32.txt"
+    default_steps = 200
     NRHS = 64
     ktype = "TF32"
 
@@ -503,6 +506,7 @@ class Precision(Multi):
     name = "precision"
     config_id = 4
     profile = "sart_multi_tiny64_bf16.txt"
+    default_steps = 100
     iters = 500
     lam = 1.0
     ktype = "TBF16"
@@ -583,6 +587,7 @@ class Warmstart(Multi):
     name = "warmstart"
     config_id = 5
     profile = "sart_multi_tiny64_fp32.txt"
+    default_steps = 5
     iters = 30000  # iteration cap
     lam = 1.0
     metric = "split-SART reconstructions to relative residual 1e-3 per second"
@@ -912,7 +917,9 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps; default: the workload's, long enough (about 0.2 s or more) for the clock "
+                         "sampler to see the GPU under load; 3 for the reference arm")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="realistic")
@@ -921,6 +928,8 @@ def main():
     ap.add_argument("--slices", type=int, default=256, help="batch workload: number of slices (first n of the 256)")
     args = ap.parse_args()
     Batch.n_slices = max(1, min(256, args.slices))
+    if args.steps is None:
+        args.steps = 3 if args.impl == "reference" else WORKLOADS[args.workload].default_steps
     if args.impl == "reference":
         run_reference(args)
     else:
