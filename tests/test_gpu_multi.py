@@ -107,3 +107,40 @@ def test_multi_rhs_queue_refills_slots(ss):
         f = osplit.recombine(f12[r, :, 0], f12[r, :, 1])
         f_ref = osplit.recombine(ref["f1"], ref["f2"])
         assert np.linalg.norm(f - f_ref) <= 1e-10 * np.linalg.norm(f_ref), r
+
+
+@pytest.mark.parametrize("n,rc", [(13, 4), (1, 2), (61, 4)])
+def test_multi_rhs_ragged_counts(ss, case, n, rc):
+    """Right-hand-side counts that leave slots empty in the last CTA."""
+    g, A1, A2, ps = case
+    system = ss.fold_system(ss.make_geometry(g), ss.F64)
+    infos, f12 = run(ss, system, ps[:n], 40, 1.0, rc=rc)
+    for r in sorted({0, n // 2, n - 1}):
+        p1, p2 = osplit.fold_rhs(ps[r])
+        ref = osart.split_sart(A1, A2, p1, p2, 1.0, 40)
+        assert infos[r]["iters"] == 40
+        f = osplit.recombine(f12[r, :, 0], f12[r, :, 1])
+        f_ref = osplit.recombine(ref["f1"], ref["f2"])
+        assert np.linalg.norm(f - f_ref) <= 1e-10 * np.linalg.norm(f_ref), r
+
+
+def test_multi_rhs_already_converged_start_stops_at_zero(ss, case):
+    """A right-hand side whose start already meets tol stops at k = 0 and returns its start unchanged."""
+    g, A1, A2, ps = case
+    system = ss.fold_system(ss.make_geometry(g), ss.F64)
+    p1, p2 = osplit.fold_rhs(ps[3])
+    ref = osart.split_sart(A1, A2, p1, p2, 1.0, 400)
+    tol = ref["rho"] * 1.5  # the 400-iteration iterate meets it
+    vt = system.vec_dtype
+    p12 = torch.empty(2, system.Mh, 2, dtype=vt, device="cuda")
+    for k in range(2):
+        ss.fold_rhs(system, torch.as_tensor(ps[3], dtype=vt, device="cuda"), p12[k])
+    f12 = torch.zeros(2, system.Nh, 2, dtype=vt, device="cuda")
+    f12[0, :, 0] = torch.as_tensor(ref["f1"], dtype=vt)
+    f12[0, :, 1] = torch.as_tensor(ref["f2"], dtype=vt)
+    start = f12[0].clone()
+    info = torch.zeros(2 * ctypes.sizeof(ss.SolveInfo), dtype=torch.uint8, device="cuda")
+    ss.solve_multi(system, p12, f12, ss.solve_opts(1000, 1.0, tol), info, rhs_per_cta=1)
+    infos = ss.read_infos(info, 2)
+    assert infos[0]["iters"] == 0 and torch.equal(f12[0], start)
+    assert infos[1]["iters"] > 0 and infos[1]["rho"] <= tol

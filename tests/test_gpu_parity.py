@@ -199,6 +199,19 @@ def test_zero_iterations_returns_f0_and_initial_residual(ss, tiny):
     assert info["iters"] == 0 and np.all(f == 0) and info["rho"] == pytest.approx(1.0, rel=1e-14)
 
 
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4])
+def test_start_that_meets_tol_stops_at_zero(ss, tiny, kernel):
+    """A start that already meets tol returns unchanged with iters = 0, whatever the kernel."""
+    geom = ss.make_geometry(tiny.g)
+    sysm = ss.fold_system(geom, ss.F64)
+    ref = osart.split_sart(tiny.A1, tiny.A2, tiny.p1, tiny.p2, 1.0, 300)
+    f0 = osplit.recombine(ref["f1"], ref["f2"])
+    info, f12, f = run_solve(ss, sysm, tiny.p, 1000, 1.0, tol=1.5 * ref["rho"], f0=f0, kernel=kernel)
+    assert info["iters"] == 0 and info["status"] == 0
+    assert info["rho"] <= 1.5 * ref["rho"]
+    assert rel(f, f0) <= 1e-14
+
+
 def test_project_matches_oracle(ss, tiny):
     geom = ss.make_geometry(tiny.g)
     for dt, tol in ((ss.F64, 1e-12), (ss.F32, 1e-6)):
