@@ -370,7 +370,8 @@ int splitsart_solve_result(splitsart_system* sys, splitsart_solve_info* info);
  * Larger systems (Mh > 65536) are rejected with SPLITSART_ERR_ARG; use
  * splitsart_solve for them.
  *
- * Arguments, all device pointers owned by the caller:
+ * Arguments, all device pointers owned by the caller and never NULL (also
+ * not when S = 0; SPLITSART_ERR_ARG otherwise):
  * - rp_dev[Mh+1] int32, col_dev[S] int32, val_dev[S] float2 (a1, a2): the
  *   folded CSR, with columns increasing within a row;
  * - cp_dev[Nh+1] int32, row_dev[S] int32, valT_dev[S] float2: the folded CSC,
@@ -382,8 +383,11 @@ int splitsart_solve_result(splitsart_system* sys, splitsart_solve_info* info);
  *   completes. status is SPLITSART_ERR_TIMEOUT if a barrier wait ran out.
  * `opts` is read as in splitsart_solve.
  *
- * The first call made with a device current looks up the array's device
- * address on that device. Make that first call before any stream capture.
+ * Every call looks up the array's device address in the current device's
+ * context (a host-side lookup; after a context is destroyed and created
+ * again the array may move, and the next call finds it). The first call in
+ * a context also loads the library's device code there: make that first
+ * call before any stream capture.
  * Every call shares the one array and clears its control block on `stream`.
  * Calls that overlap on the GPU (other streams, other host threads) race on
  * the array and must be serialised by the caller.

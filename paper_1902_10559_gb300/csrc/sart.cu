@@ -37,7 +37,6 @@
 #include <cstdio>
 #include <algorithm>
 #include <initializer_list>
-#include <mutex>
 #include <vector>
 #include <type_traits>
 
@@ -1910,7 +1909,6 @@ namespace splitsart {
 namespace {
 
 constexpr int kStaticMaxRows = 65536;
-constexpr int kMaxDevices = 64;
 
 struct StaticScratch {
     LaunchCtl ctl;  // cleared at every call
@@ -1921,24 +1919,17 @@ struct StaticScratch {
 
 static __device__ __align__(256) unsigned char g_static_scratch[sizeof(StaticScratch)];
 
-std::mutex g_static_mu;
-void* g_static_addr[kMaxDevices] = {};
-
-// Device address of g_static_scratch on the current device. It is looked up
-// once per device, on the first call made with that device current.
+// Device address of g_static_scratch in the current device's context. In host
+// code the array's name is only a host-side stand-in, so the address is looked
+// up on every call: a context that was torn down and created again (after
+// cudaDeviceReset, say) reloads the library's device code, and the array may
+// then sit at another address. The lookup is a host-side table read once the
+// device code is loaded; the first call in a context also loads it.
 int static_scratch_address(StaticScratch** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "solve_static: cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) return fail(SPLITSART_ERR_ARG, "solve_static: device %d out of range", dev);
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
-        void* ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "solve_static: cudaGetSymbolAddress");
-        g_static_addr[dev] = ptr;
-    }
-    *out = reinterpret_cast<StaticScratch*>(g_static_addr[dev]);
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "solve_static: cudaGetSymbolAddress");
+    *out = reinterpret_cast<StaticScratch*>(ptr);
     return SPLITSART_OK;
 }
 
@@ -2032,7 +2023,8 @@ extern "C" int splitsart_solve_static(int64_t Mh, int64_t Nh, const int32_t* rp_
                                       splitsart_solve_info* info_dev, void* stream) {
     splitsart::NvtxRange nvtx_range("splitsart_solve_static");
     using namespace splitsart;
-    if (!opts || !info_dev || !rp_dev || !cp_dev || !p12_dev || !f12_dev || !invR_dev || !invC_dev)
+    if (!opts || !info_dev || !rp_dev || !col_dev || !val_dev || !cp_dev || !row_dev || !valT_dev || !p12_dev ||
+        !f12_dev || !invR_dev || !invC_dev)
         return fail(SPLITSART_ERR_ARG, "solve_static: NULL argument");
     if (Mh <= 0 || Nh <= 0) return fail(SPLITSART_ERR_ARG, "solve_static: Mh and Nh must be positive");
     if (Mh > kStaticMaxRows)

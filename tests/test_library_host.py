@@ -114,3 +114,22 @@ def test_from_csr_validation(ss):
     assert e.value.code == ss.ERR_ODD_DIM
     g = ss.make_geometry_from_csr(4, 6, rp, np.array([1, 2, 0]), np.ones(3))
     assert (g.M, g.N, g.nnz_half) == (4, 6, 3)
+
+
+def test_static_solve_rejects_null_matrix_pointers(ss):
+    """splitsart_solve_static checks every caller pointer before it touches the device.
+
+    The check runs on the host, so a NULL matrix pointer is an argument error,
+    not a device fault, and no GPU is needed to see it.
+    """
+    import ctypes
+    h = ss.lib()
+    opts = ss.solve_opts(5, 1.0)
+    good = 256  # any non-NULL value: the call must return before dereferencing anything
+    names = ["rp", "col", "val", "cp", "row", "valT", "invR", "invC", "p12", "f12"]
+    for k, name in enumerate(names):
+        ptrs = [good] * len(names)
+        ptrs[k] = None
+        rc = h.splitsart_solve_static(16, 8, *ptrs, ctypes.byref(opts), good, None)
+        assert rc == ss.ERR_ARG, name
+        assert "NULL" in ss.last_error(), name
