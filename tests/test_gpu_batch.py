@@ -12,6 +12,7 @@ from oracle import geometry as ogeo
 from oracle import sart as osart
 from oracle import split as osplit
 from paper_1902_10559_gb300.synthetic import TINY, Geometry, batch_geometries, covering_detector_width, random_phantom
+from tests.parity import close, close_scalar
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -35,10 +36,6 @@ def small_geometry(nx, nz, K, nb):
 
 SMALL = [TINY, small_geometry(8, 6, 4, 20), small_geometry(16, 10, 6, 34), small_geometry(24, 8, 8, 50),
          small_geometry(10, 12, 5, 26)]
-
-
-def rel(a, b):
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
 def oracle_case(g, seed):
@@ -83,11 +80,12 @@ def test_batch_matches_single_slices_and_oracle(ss, dt, tol):
         ref = osart.split_sart(A1, A2, p1, p2, 0.9, 40)
         fk = f[off["N"][k]:off["N"][k + 1]]
         assert infos[k]["iters"] == 40 and infos[k]["status"] == 0
-        assert rel(fk, osplit.recombine(ref["f1"], ref["f2"])) <= tol, (k, rel(fk, osplit.recombine(ref["f1"], ref["f2"])))
-        assert abs(infos[k]["rho"] - ref["rho"]) <= tol * ref["rho"]
+        close(fk, osplit.recombine(ref["f1"], ref["f2"]), tol, f"slice {k} ({dt})")
+        close_scalar(infos[k]["rho"], ref["rho"], tol, f"rho of slice {k}")
         single = ss.fold_system(geo, dtc)
         _, fs = solve(ss, single, torch.as_tensor(pk, dtype=batch.vec_dtype, device="cuda"), 40, 0.9, kernel=1)
-        assert rel(fk, fs) <= (1e-13 if dt == "f64" else 1e-6)
+        # Two kernels with different summation orders: equal up to rounding (FP32: a few ulps per iteration).
+        close(fk, fs, 1e-13 if dt == "f64" else 1e-5, f"slice {k} in the batch vs alone")
 
 
 def test_batch_stops_each_slice_on_its_own(ss):
@@ -103,7 +101,7 @@ def test_batch_stops_each_slice_on_its_own(ss):
     for k, c in enumerate(cases):
         assert infos[k]["iters"] == expect[k], (k, infos[k], expect[k])
         ref = osart.split_sart(c[2], c[3], c[4], c[5], 1.0, 60, tol=tol)
-        assert rel(f[off["N"][k]:off["N"][k + 1]], osplit.recombine(ref["f1"], ref["f2"])) <= 1e-10
+        close(f[off["N"][k]:off["N"][k + 1]], osplit.recombine(ref["f1"], ref["f2"]), 1e-10, f"slice {k} at its stop")
 
 
 def test_batch_layouts_and_projection(ss):
@@ -117,7 +115,7 @@ def test_batch_layouts_and_projection(ss):
     for k, g in enumerate(SMALL):
         A = ogeo.mirrored_system_matrix(g)
         pk = p[off["M"][k]:off["M"][k + 1]].cpu().numpy()
-        assert rel(pk, A @ ogeo.image_to_snake(g, imgs[k])) <= 1e-12
+        close(pk, A @ ogeo.image_to_snake(g, imgs[k]), 1e-12, f"p of slice {k}")
     # fold_image then recombine(image layout) is the identity (up to one rounding).
     f12 = torch.empty(batch.Nh, 2, dtype=torch.float64, device="cuda")
     ss.fold_image(batch, f_img, f12, layout=ss.LAYOUT_IMAGE)
@@ -128,33 +126,42 @@ def test_batch_layouts_and_projection(ss):
 
 @pytest.mark.slow
 def test_full_batch_sampled_slices(ss):
-    """The 256-slice workload (nx in {256..1024}, nz in [64, 256], K in [16, 32], nb = 2 nx), 20 iterations.
+    """The 256-slice workload (nx in {256..1024}, nz in [64, 256], K in [16, 32], nb = 2 nx), 20 iterations, FP32.
 
-    Sampled slices are checked against single-slice solves, and the smallest
-    against the oracle.
+    The smallest slice, the largest and 4 seeded random others are checked
+    against the oracle, element by element at 1e-4. Their projections are the
+    oracle's (FP64 A f of its own Siddon matrix, rounded to FP32 for the
+    device); the other slices take device projections, which only fill the
+    batch. The largest slices are where the row-streaming kernel's chunking
+    and the per-slice stop tests are stressed.
     """
     gs = batch_geometries()
-    geoms = [ss.make_geometry(g) for g in gs]
+    geoms = ss.make_geometries_device(gs)
     batch = ss.fold_batch(geoms, ss.F32)
     off = ss.system_slices(batch)
-    f_img = torch.cat([torch.as_tensor(random_phantom(g, 3, 12, stream=k).reshape(-1), dtype=torch.float32)
-                       for k, g in enumerate(gs)]).cuda()
+    imgs = [random_phantom(g, 3, 12, stream=k) for k, g in enumerate(gs)]
+    f_img = torch.cat([torch.as_tensor(im.reshape(-1), dtype=torch.float32) for im in imgs]).cuda()
     p = torch.empty(batch.M, device="cuda")
     ss.project(batch, f_img, p, layout=ss.LAYOUT_IMAGE)
+    sizes = [g.N for g in gs]
+    first, last = int(np.argmin(sizes)), int(np.argmax(sizes))
+    rng = np.random.default_rng(1902_10559)
+    others = [k for k in range(len(gs)) if k not in (first, last)]
+    picks = [first, last] + sorted(int(k) for k in rng.choice(others, 4, replace=False))
+    cases = {}
+    for k in picks:
+        g = gs[k]
+        A = ogeo.mirrored_system_matrix(g)
+        pk = (A @ ogeo.image_to_snake(g, imgs[k])).astype(np.float32)
+        p[off["M"][k]:off["M"][k + 1]] = torch.as_tensor(pk, device="cuda")
+        cases[k] = (A, pk.astype(np.float64))
     infos, f = solve(ss, batch, p, 20, 0.8)
     assert all(i["iters"] == 20 and i["status"] == 0 for i in infos)
-    sizes = [g.N for g in gs]
-    picks = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 17, 131})
     for k in picks:
-        single = ss.fold_system(geoms[k], ss.F32)
-        pk = p[off["M"][k]:off["M"][k + 1]].contiguous()
-        _, fs = solve(ss, single, pk, 20, 0.8, kernel=1)
-        assert rel(f[off["N"][k]:off["N"][k + 1]], fs) <= 1e-6, k
-    k = int(np.argmin(sizes))
-    g = gs[k]
-    A = ogeo.mirrored_system_matrix(g)
-    A1, A2 = osplit.fold_matrix(A)
-    pk = p[off["M"][k]:off["M"][k + 1]].double().cpu().numpy()
-    p1, p2 = osplit.fold_rhs(pk)
-    ref = osart.split_sart(A1, A2, p1, p2, 0.8, 20)
-    assert rel(f[off["N"][k]:off["N"][k + 1]], osplit.recombine(ref["f1"], ref["f2"])) <= 1e-4
+        A, pk = cases[k]
+        A1, A2 = osplit.fold_matrix(A)
+        p1, p2 = osplit.fold_rhs(pk)
+        ref = osart.split_sart(A1, A2, p1, p2, 0.8, 20)
+        close(f[off["N"][k]:off["N"][k + 1]], osplit.recombine(ref["f1"], ref["f2"]), 1e-4,
+              f"batch slice {k} (N = {gs[k].N})")
+        close_scalar(infos[k]["rho"], ref["rho"], 1e-4, f"rho of slice {k}")

@@ -1,13 +1,18 @@
-"""Device tracer (splitsart_make_geometries_device) against the host tracer.
+"""Device tracer (splitsart_make_geometries_device) against the oracle and the host tracer.
 
-The two trace the same rays with the same FP64 expressions (Section 2
-geometry, Siddon lengths), so the rows must be equal bit for bit: the same
-row pointers, columns and lengths. The host tracer is pinned to the oracle's
-geometry in test_library_host.py.
+- Against the oracle's Siddon tracer (oracle.geometry, written separately in
+  NumPy): the same cells in the same order, lengths within 1e-12 relative,
+  on every ray of the tiny slice, of a skewed slice and of a slice with a
+  vertical ray on a cell boundary, and on 300 sampled
+  rays of the realistic slice and of three batch slices.
+- Against the library's host tracer: the two trace the same rays with the
+  same FP64 expressions (Section 2 geometry, Siddon lengths), so the rows
+  must be equal bit for bit: the same row pointers, columns and lengths.
 """
 import numpy as np
 import pytest
 
+from oracle import geometry as ogeo
 from paper_1902_10559_gb300.synthetic import REALISTIC, TINY, Geometry, batch_geometries
 
 pytestmark = pytest.mark.gpu
@@ -39,6 +44,37 @@ def assert_same_rows(a, b):
     assert np.array_equal(ra, rb)
     assert np.array_equal(ca, cb)
     assert np.array_equal(va.view(np.uint64), vb.view(np.uint64))  # bit for bit
+
+
+def assert_rows_match_oracle(dev, g, rows):
+    """Rows of a device-traced geometry against oracle.geometry.siddon_ray, traced ray by ray."""
+    rp, col, val = dev.export()
+    assert dev.M == g.M and dev.N == g.N and len(rp) == g.M // 2 + 1
+    src = ogeo.source_positions(g)
+    det = ogeo.detector_centres(g)
+    for i in rows:
+        k, b = divmod(int(i), g.nb)
+        j, w = ogeo.siddon_ray(g, src[k], np.array([det[b], 0.0]))
+        got_j, got_w = col[rp[i]:rp[i + 1]], val[rp[i]:rp[i + 1]]
+        assert np.array_equal(got_j, j), (g, i)
+        assert np.all(np.abs(got_w - w) <= 1e-12 * np.maximum(np.abs(w), 1.0)), (g, i, np.abs(got_w - w).max())
+
+
+@pytest.mark.parametrize("g", [TINY, SKEW, ON_PLANE], ids=["tiny", "skew", "on_plane"])
+def test_device_tracer_matches_oracle_every_ray(ss, g):
+    (dev,) = ss.make_geometries_device([g])
+    assert_rows_match_oracle(dev, g, range(g.M // 2))
+
+
+def test_device_tracer_matches_oracle_sampled_rays(ss):
+    """300 seeded rays of the realistic slice and of three batch slices (smallest, largest, one other)."""
+    bg = batch_geometries()
+    sizes = [x.N for x in bg]
+    gs = [REALISTIC, bg[int(np.argmin(sizes))], bg[int(np.argmax(sizes))], bg[17]]
+    devs = ss.make_geometries_device(gs)
+    rng = np.random.default_rng(2)
+    for g, d in zip(gs, devs):
+        assert_rows_match_oracle(d, g, rng.choice(g.M // 2, 300, replace=False))
 
 
 @pytest.mark.parametrize("g", [TINY, SKEW, ON_PLANE, REALISTIC], ids=["tiny", "skew", "on_plane", "realistic"])

@@ -7,11 +7,13 @@ import ctypes
 
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 from oracle import geometry as ogeo
 from oracle import sart as osart
 from oracle import split as osplit
 from paper_1902_10559_gb300.synthetic import TINY, random_phantom
+from tests.parity import close, close_norm
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -51,18 +53,33 @@ def run(ss, system, ps, iters, lam, tol=0.0, rc=0):
     return ss.read_infos(info, n), f12.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("dt,tol,rc", [("f64", 1e-10, 4), ("f32", 1e-4, 1), ("f32", 1e-4, 8), ("bf16", 2e-3, 16)])
+@pytest.mark.parametrize("dt,tol,rc", [("f64", 1e-10, 4), ("f32", 1e-4, 1), ("f32", 1e-4, 8), ("bf16", 1e-4, 16)])
 def test_multi_rhs_matches_oracle(ss, case, dt, tol, rc):
+    """Each right-hand side against the oracle, element by element.
+
+    For BF16 values the oracle runs on the stored (dequantised) matrix, which
+    isolates the kernel's FP32 arithmetic; the storage format's own error
+    against the exact matrix is bounded norm-wise at 2e-3.
+    """
     g, A1, A2, ps = case
     system = ss.fold_system(ss.make_geometry(g), ss.DTYPE_NAMES[dt])
+    B1, B2 = A1, A2
+    if dt == "bf16":
+        out = system.export()
+        shape = (g.M // 2, g.N // 2)
+        B1 = sp.csr_matrix((out["a1"], out["col"], out["row_ptr"]), shape=shape)
+        B2 = sp.csr_matrix((out["a2"], out["col"], out["row_ptr"]), shape=shape)
     infos, f12 = run(ss, system, ps, 100, 1.0, rc=rc)
     for r in (0, 1, 17, 63):
         p1, p2 = osplit.fold_rhs(ps[r])
-        ref = osart.split_sart(A1, A2, p1, p2, 1.0, 100)
+        ref = osart.split_sart(B1, B2, p1, p2, 1.0, 100)
         f_ref = osplit.recombine(ref["f1"], ref["f2"])
         f = osplit.recombine(f12[r, :, 0], f12[r, :, 1])
         assert infos[r]["iters"] == 100 and infos[r]["status"] == 0
-        assert np.linalg.norm(f - f_ref) / np.linalg.norm(f_ref) <= tol, r
+        close(f, f_ref, tol, f"right-hand side {r} ({dt}, {rc} per CTA)")
+        if dt == "bf16":
+            exact = osart.split_sart(A1, A2, p1, p2, 1.0, 100)
+            close_norm(f, osplit.recombine(exact["f1"], exact["f2"]), 2e-3, f"right-hand side {r}: BF16 storage")
 
 
 def test_multi_rhs_stop_individually(ss, case):
@@ -106,7 +123,7 @@ def test_multi_rhs_queue_refills_slots(ss):
         assert iters[r] == ref["iters"], r
         f = osplit.recombine(f12[r, :, 0], f12[r, :, 1])
         f_ref = osplit.recombine(ref["f1"], ref["f2"])
-        assert np.linalg.norm(f - f_ref) <= 1e-10 * np.linalg.norm(f_ref), r
+        close(f, f_ref, 1e-10, f"right-hand side {r} after refills")
 
 
 @pytest.mark.parametrize("n,rc", [(13, 4), (1, 2), (61, 4)])
@@ -121,7 +138,7 @@ def test_multi_rhs_ragged_counts(ss, case, n, rc):
         assert infos[r]["iters"] == 40
         f = osplit.recombine(f12[r, :, 0], f12[r, :, 1])
         f_ref = osplit.recombine(ref["f1"], ref["f2"])
-        assert np.linalg.norm(f - f_ref) <= 1e-10 * np.linalg.norm(f_ref), r
+        close(f, f_ref, 1e-10, f"right-hand side {r} of {n}")
 
 
 def test_multi_rhs_already_converged_start_stops_at_zero(ss, case):

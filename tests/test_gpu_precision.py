@@ -6,9 +6,11 @@ with FP32 accumulation. The normalisers and the residual test are FP64.
 - Codes: bit-exact against the oracle's quantiser. Both divide in FP32 and
   round to nearest even.
 - Kernel parity: the GPU solve on the stored values against the oracle's FP64
-  SART on the same dequantised matrix, at 1e-4 (FP32 accumulation).
-- Total error: against the FP64 oracle on the exact matrix, at 2e-3. Both
-  errors are printed per result.
+  SART on the same dequantised matrix, at 1e-4 (FP32 accumulation), element
+  by element.
+- Total error: against the FP64 oracle on the exact matrix, at 2e-3
+  norm-wise. This is the storage format's error (BF16 keeps 8 mantissa bits),
+  not the kernel's; its worst element is printed beside it.
 """
 import numpy as np
 import pytest
@@ -19,6 +21,7 @@ from oracle import quant as oquant
 from oracle import sart as osart
 from oracle import split as osplit
 from paper_1902_10559_gb300.synthetic import TINY, random_phantom
+from tests.parity import close, close_norm, close_scalar
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -43,10 +46,6 @@ def tiny():
     A1, A2 = osplit.fold_matrix(A)
     p1, p2 = osplit.fold_rhs(p)
     return g, A, p, A1, A2, p1, p2
-
-
-def rel(a, b):
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
 @pytest.mark.parametrize("fmt", ["bf16", "f16"])
@@ -89,11 +88,8 @@ def test_reduced_precision_solve(ss, tiny, fmt):
     fg = f.cpu().numpy().astype(np.float64)
     f_hat = osplit.recombine(ref_hat["f1"], ref_hat["f2"])
     f_exact = osplit.recombine(ref_exact["f1"], ref_exact["f2"])
-    kernel_err = rel(fg, f_hat)
-    total_err = rel(fg, f_exact)
-    print(f"{fmt}: kernel error vs oracle on stored values {kernel_err:.3e}; total error vs exact FP64 {total_err:.3e}; "
-          f"rho {info['rho']:.6e} (oracle on stored {ref_hat['rho']:.6e}, exact {ref_exact['rho']:.6e})")
+    print(f"{fmt}: rho {info['rho']:.6e} (oracle on stored {ref_hat['rho']:.6e}, exact {ref_exact['rho']:.6e})")
     assert info["iters"] == iters
-    assert kernel_err <= 1e-4
-    assert total_err <= 2e-3
-    assert abs(info["rho"] - ref_hat["rho"]) <= 1e-4 * ref_hat["rho"]
+    close(fg, f_hat, 1e-4, f"{fmt}: kernel error vs oracle on the stored values")
+    close_norm(fg, f_exact, 2e-3, f"{fmt}: total error vs exact FP64 (storage format)")
+    close_scalar(info["rho"], ref_hat["rho"], 1e-4, "rho vs oracle on the stored values")

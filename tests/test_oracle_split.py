@@ -146,3 +146,42 @@ def test_odd_sizes_rejected():
         split.fold_matrix(np.zeros((3, 4)))
     with pytest.raises(ValueError):
         split.fold_rhs(np.zeros(5))
+
+
+def test_folded_pattern_size_example1_keeps_the_cancelled_zero():
+    """Example 1: all 2 x 3 folded positions are stored, including A1[0, 0] = 1 - 1 = 0.
+
+    The union pattern counts a position when w_ij or w_{M-1-i,j} is stored, so the
+    zero that cancellation makes in the printed A1 (Eq. 14) still counts: S = 6.
+    """
+    import scipy.sparse as sp
+    A = sp.csr_matrix(EX1["A"])
+    assert split.folded_pattern_size(A) == 6
+    assert EX1["A1"][0, 0] == 0.0  # the printed zero is a cancellation, not a missing entry
+
+
+@pytest.mark.parametrize("rows,expect", [
+    # One stored pair per row that cancels in A1: kept (1 position), the other half of the row is empty.
+    ([[1.0, 0.0, 0.0, 1.0]], 1),
+    # Entries only in the right half: their reflections land in distinct folded columns.
+    ([[0.0, 0.0, 2.0, 3.0]], 2),
+    # A left entry and the reflection of a right entry in the same folded column count once.
+    ([[5.0, 0.0, 0.0, 7.0]], 1),
+    # Two rows of a 4 x 4 matrix: row 0 fills both folded columns, row 1 only the reflected column 0.
+    ([[1.0, 2.0, 0.0, 0.0], [0.0, 0.0, 0.0, 4.0]], 3),
+    # An empty folded row contributes nothing.
+    ([[0.0, 0.0, 0.0, 0.0], [0.0, 1.0, 1.0, 0.0]], 1),
+])
+def test_folded_pattern_size_hand_counts(rows, expect):
+    """Hand-counted union patterns of small matrices that satisfy Eq. (2).
+
+    Each top row i is given; row M-1-i is its reflection w[M-1-i, N-1-j] = w[i, j].
+    Position (i, j), j < N/2, is stored when w[i, j] != 0 or w[i, N-1-j] != 0.
+    """
+    import scipy.sparse as sp
+    top = np.array(rows, dtype=float)
+    A = np.vstack([top, top[::-1, ::-1]])
+    assert np.array_equal(A, A[::-1, ::-1])
+    assert split.folded_pattern_size(sp.csr_matrix(A)) == expect
+    # The count is a property of the stored pattern, not of the values: scaling cannot change it.
+    assert split.folded_pattern_size(sp.csr_matrix(-3.0 * A)) == expect

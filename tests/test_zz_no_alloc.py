@@ -16,6 +16,7 @@ import pytest
 
 from oracle import geometry as ogeo
 from paper_1902_10559_gb300.synthetic import REALISTIC, TINY, random_phantom
+from tests.parity import close
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -79,8 +80,8 @@ def test_static_solve_matches_regular_solve_twice(ss, g, cfg, iters):
         torch.cuda.synchronize()
         got = ss.read_info(info)
         assert got["status"] == 0 and got["iters"] == ref["iters"] == iters, (call, got, ref)
-        err = (torch.linalg.norm((f - f_ref).double()) / torch.linalg.norm(f_ref.double())).item()
-        assert err <= 1e-4, (call, err)
+        # A different kernel from the regular solve's, so equal up to FP32 rounding, element by element.
+        close(f.cpu().numpy(), f_ref.cpu().numpy(), 1e-4, f"call {call}: static solve vs regular solve")
         assert abs(got["rho"] - ref["rho"]) <= 1e-4 * ref["rho"], (call, got["rho"], ref["rho"])
 
 
