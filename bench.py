@@ -123,9 +123,13 @@ def read_peak(key: str, fallback: float):
         return fallback, "fallback"
 
 
-def profile_traffic(name: str, src: str = KERNEL_SRC):
+def profile_traffic(name: str, src: str = KERNEL_SRC, algorithmic_bytes: float | None = None):
     """Per-launch DRAM bytes of the solve kernel from a committed ncu summary.
 
+    A summary gives either ``dram_bytes_per_launch`` (captured on the bench's
+    own launch) or ``dram_over_algorithmic`` (captured on a smaller case of the
+    same kernel whose traffic grows with its algorithmic bytes; it is then
+    scaled by ``algorithmic_bytes``, the bench launch's).
     Returns None if the summary is absent, or if the kernel's source file
     (``src``) has changed since it was taken.
     """
@@ -135,10 +139,15 @@ def profile_traffic(name: str, src: str = KERNEL_SRC):
         return None
     src_hash = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
-    m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not m_hash or not m_bytes or m_hash.group(1) != src_hash:
+    if not m_hash or m_hash.group(1) != src_hash:
         return None
-    return float(m_bytes.group(1))
+    m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if m_bytes:
+        return float(m_bytes.group(1))
+    m_ratio = re.search(r"dram_over_algorithmic:\s*([0-9.eE+]+)", txt)
+    if m_ratio and algorithmic_bytes:
+        return float(m_ratio.group(1)) * algorithmic_bytes
+    return None
 
 
 def algorithmic_bytes_per_launch(S, Mh, Nh, iters, batch_rows=0):
@@ -234,12 +243,19 @@ class Realistic:
         alg = algorithmic_bytes_per_launch(S, Mh, Nh, self.iters)
         peak, kind = read_peak("hbm_gbs", 6800.0)
         ach = alg / (solve_ms / 1e3) / 1e9
-        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": profile_traffic(self.profile),
-                "kernel": "sart_resident_kernel<TF32,LPC> (matrix slice kept in shared memory)"
-                          if self.tuned.get("kernel") == 2 else "sart_stream_kernel<TF32,LPC>",
-                "algorithmic_bytes_per_launch": alg, "peak_source": f"{kind} hbm_gbs",
-                "note": "per-iteration working set ~35 MB is L2/shared-memory resident within a solve"}
+        traffic = profile_traffic(self.profile)
+        out = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+               "traffic": traffic,
+               "kernel": "sart_resident_kernel<TF32,LPC> (matrix slice kept in shared memory)"
+                         if self.tuned.get("kernel") == 2 else "sart_stream_kernel<TF32,LPC>",
+               "algorithmic_bytes_per_launch": alg, "peak_source": f"{kind} hbm_gbs",
+               "achieved_is": "effective bandwidth: algorithmic bytes of the solve / solve time. The per-iteration "
+                              "working set (about 35 MB) stays in shared memory and L2, so this is not DRAM "
+                              "traffic; dram_gbs is"}
+        if traffic:
+            out["dram_gbs"] = traffic / (solve_ms / 1e3) / 1e9
+            out["dram_frac"] = out["dram_gbs"] / peak
+        return out
 
     def extra(self, ss):
         """Workload-specific keys added to the JSON line."""
@@ -298,7 +314,7 @@ class Batch(Realistic):
     name = "batch"
     two_process_baseline = False
     config_id = 3
-    profile = "sart_rows_batch256_fp32.txt"
+    profile = "sart_rows_batch16_fp32.txt"
     default_steps = 10
     n_slices = 256
 
@@ -364,24 +380,32 @@ class Batch(Realistic):
         # The timed graph also holds fold_rhs and recombine (about 0.1% of its bytes).
         peak, kind = read_peak("hbm_gbs", 6800.0)
         ach = alg / (solve_ms / 1e3) / 1e9
-        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": profile_traffic(self.profile), "kernel": self.kernel_name(),
-                "algorithmic_bytes_per_launch": alg, "peak_source": f"{kind} hbm_gbs",
-                "note": "timed region = the replayed graph (fold of p, solve, recombine); inputs far exceed L2"}
+        traffic = profile_traffic(self.profile, algorithmic_bytes=alg)
+        out = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+               "traffic": traffic, "kernel": self.kernel_name(),
+               "algorithmic_bytes_per_launch": alg, "peak_source": f"{kind} hbm_gbs",
+               "traffic_source": "ncu DRAM counters of the 16-slice case (one launch), scaled to this launch by "
+                                 "algorithmic bytes",
+               "note": "timed region = the replayed graph (fold of p, solve, recombine); inputs far exceed L2"}
+        if traffic:
+            out["dram_gbs"] = traffic / (solve_ms / 1e3) / 1e9
+            out["dram_frac"] = out["dram_gbs"] / peak
+        return out
 
-    def extra(self, ss):
+    def extra(self, ss, host_tracer=True):
         # Setup, outside the timed steps: the first-half rows of all slices
-        # traced on the GPU, and on the host cores for comparison.
+        # traced on the GPU, and (host_tracer) on the host cores for comparison.
         import torch
-        t0 = time.perf_counter()
-        host = [ss.make_geometry(g) for g in self.gs]
-        t1 = time.perf_counter()
-        sysm = ss.fold_batch(host, ss.F32)
-        torch.cuda.synchronize()
-        self.geometry_s["host_tracer"] = t1 - t0
-        self.geometry_s["host_tracer_and_fold"] = time.perf_counter() - t0
-        self.geometry_s["host_threads"] = min(32, os.cpu_count() or 1)
-        del host, sysm
+        if host_tracer:
+            t0 = time.perf_counter()
+            host = [ss.make_geometry(g) for g in self.gs]
+            t1 = time.perf_counter()
+            sysm = ss.fold_batch(host, ss.F32)
+            torch.cuda.synchronize()
+            self.geometry_s["host_tracer"] = t1 - t0
+            self.geometry_s["host_tracer_and_fold"] = time.perf_counter() - t0
+            self.geometry_s["host_threads"] = min(32, os.cpu_count() or 1)
+            del host, sysm
         return {"forms": self.form_times(ss, self.geoms), "geometry_s": self.geometry_s}
 
     def kernel_name(self):
@@ -527,21 +551,13 @@ class Precision(Multi):
         self.info = self.system.info()
         self.opts = ss.solve_opts(self.iters, self.lam, block_threads=self.tuned["block_threads"])
 
-    def extra(self, ss):
+    def time_to_tol(self, ss):
+        """Per storage form: the launch time and iterations of the 64 right-hand sides to rho <= 1e-3."""
         import numpy as np
         import torch
         out = {}
-        finals = {}
         for name, (sysm, tuned) in self.forms.items():
-            # 500 iterations, for the distance between forms.
             f12 = torch.zeros_like(self.f12)
-            ss.solve_multi(sysm, self.p12, f12, ss.solve_opts(self.iters, self.lam,
-                                                              block_threads=tuned["block_threads"]),
-                           self.infobuf, rhs_per_cta=tuned["rhs_per_cta"])
-            img = torch.empty(self.NRHS * self.g.N, device=f12.device)
-            ss.recombine(self.vec, f12.view(-1, 2), img, layout=ss.LAYOUT_IMAGE)
-            finals[name] = img.double()
-            # To rho <= 1e-3.
             opts = ss.solve_opts(self.MAX_ITERS, self.lam, self.TOL, block_threads=tuned["block_threads"])
             ts = []
             for _ in range(3):
@@ -558,10 +574,25 @@ class Precision(Multi):
             out[name] = {"ms": float(np.median(ts)), "iters_mean": float(its.mean()), "iters_max": int(its.max()),
                          "reached": float(reached.mean()), "launch": tuned}
         for name in ("bf16", "f16"):
+            out[name]["time_vs_plain_f32"] = out[name]["ms"] / out["f32"]["ms"]
+        return out
+
+    def extra(self, ss):
+        import torch
+        out = self.time_to_tol(ss)
+        finals = {}
+        for name, (sysm, tuned) in self.forms.items():
+            # 500 iterations, for the distance between forms.
+            f12 = torch.zeros_like(self.f12)
+            ss.solve_multi(sysm, self.p12, f12, ss.solve_opts(self.iters, self.lam,
+                                                              block_threads=tuned["block_threads"]),
+                           self.infobuf, rhs_per_cta=tuned["rhs_per_cta"])
+            img = torch.empty(self.NRHS * self.g.N, device=f12.device)
+            ss.recombine(self.vec, f12.view(-1, 2), img, layout=ss.LAYOUT_IMAGE)
+            finals[name] = img.double()
+        for name in ("bf16", "f16"):
             d = torch.linalg.vector_norm(finals[name] - finals["f32"]) / torch.linalg.vector_norm(finals["f32"])
             out[name]["rel_diff_vs_f32_at_500"] = float(d)
-        for name in ("bf16", "f16"):
-            out[name]["time_vs_f32"] = out[name]["ms"] / out["f32"]["ms"]
         return {"time_to_rho_1e-3": out,
                 "note": "64 right-hand sides, one solve_multi launch each; ms is the launch time until the last "
                         "right-hand side stops; errors against the FP64 oracle are in the precision tests"}
@@ -649,6 +680,39 @@ class Warmstart(Multi):
                 "traffic": None, "kernel": "sart_multi_kernel<TF32,RC> (the solves dominate the warm pipeline)",
                 "peak_source": "nominal FP32 FMA rate at 2.07 GHz",
                 "note": "useful FMAs of the iterations each right-hand side needed, over the whole warm pipeline"}
+
+    def time_to_tol(self, ss):
+        """The warm pipeline and the plain solve of the 512 held-out right-hand sides, each timed 3 times."""
+        import numpy as np
+        import torch
+        p12 = self.ws.fold_rhs(self.p.view(self.N_HELD, -1))
+        res = {}
+        for name in ("plain", "warm"):
+            ts = []
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                if name == "plain":
+                    _, info = self.ws.solve_plain(p12, self.TOL, self.iters)
+                else:
+                    _, e, r, picked = self.ws.solve_warm(p12, self.TOL, self.iters)
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            if name == "plain":
+                infos = ss.read_infos(info, self.N_HELD)
+                its = np.array([i["iters"] for i in infos])
+                rho = np.array([i["rho"] for i in infos])
+            else:
+                its, rho = self.ws.warm_counts(ss.read_infos(e, self.N_HELD), ss.read_infos(r, self.N_HELD), self.TOL)
+            res[name] = {"ms": float(np.median(ts)), "iters_mean": float(its.mean()),
+                         "iters_median": float(np.median(its)), "iters_max": int(its.max()),
+                         "reached": float(np.mean(rho <= self.TOL))}
+        res["warm"]["kept_guess"] = float(picked.float().mean().item())
+        res["warm"]["time_vs_plain_f32"] = res["warm"]["ms"] / res["plain"]["ms"]
+        res["warm"]["iters_vs_plain_f32"] = res["warm"]["iters_mean"] / res["plain"]["iters_mean"]
+        res["training"] = {"pairs": self.N_TRAIN, "epochs": self.EPOCHS, "seconds": self.setup_s}
+        return res
 
     def extra(self, ss):
         import numpy as np
@@ -784,6 +848,72 @@ def oracle_two_process(wl, one_process_value, budget_s):
                       f"start)"}
 
 
+def time_steps(wl, ss, steps, warmup, stream, flush, gpu_index):
+    """Warm-up, then `steps` timed steps of a set-up workload, with the clocks sampled meanwhile.
+
+    Each timed step is bracketed by CUDA events on `stream`, after an L2 flush.
+    Returns (total step ms, mean solve ms, clock summary, units of one step).
+    """
+    import torch
+    for _ in range(warmup):
+        wl.step(ss, wl.p, wl.f, ss.LAYOUT_IMAGE)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    s_solve = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_index) as clocks:
+        for k in range(steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            wl.step(ss, wl.p, wl.f, ss.LAYOUT_IMAGE, s_solve[k])
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    solve_ms = sum(a.elapsed_time(b) for a, b in s_solve) / steps
+    return step_ms, solve_ms, clocks.summary(), wl.units(ss)
+
+
+def batch_record(ss, dev, rank, stream, flush, gpu_index, steps, warmup):
+    """The 256-slice batch, timed like the main line: the HBM-bound workload of the metric."""
+    import torch
+    wl = Batch()
+    wl.setup(ss, dev, rank)
+    step_ms, solve_ms, clocks, units = time_steps(wl, ss, steps, warmup, stream, flush, gpu_index)
+    rec = {"metric": wl.metric, "value": units * steps / (step_ms / 1e3), "unit": wl.unit, "steps": steps,
+           "warmup": warmup, "ms_per_step": step_ms / steps, "dtype": wl.dtype, "config": wl.config(),
+           "roofline": wl.roofline(ss, solve_ms), "clocks": clocks,
+           "breakdown_ms": {"solve": solve_ms, "step": step_ms / steps}, "gpu_launches": wl.launches * steps}
+    rec.update(wl.extra(ss, host_tracer=False))
+    del wl
+    torch.cuda.empty_cache()
+    return rec
+
+
+def time_to_tol_record(ss, dev, rank, stream):
+    """Iterations and time to rho <= 1e-3 of each form against plain FP32 split-SART, on one GPU.
+
+    - Storage forms: FP32, BF16 and FP16 matrix values on 64 right-hand sides
+      (tiny slice geometry, lambda = 1), one solve_multi launch each.
+    - Learned warm start against plain FP32 from zero on 512 held-out
+      right-hand sides: the whole warm pipeline (5 iterations, network, fold,
+      fallback, continuation) against the plain solve.
+    """
+    import torch
+    pr = Precision()
+    pr.setup(ss, dev, rank)
+    forms = pr.time_to_tol(ss)
+    del pr
+    ws = Warmstart()
+    ws.setup(ss, dev, rank)
+    warm = ws.time_to_tol(ss)
+    del ws
+    torch.cuda.empty_cache()
+    return {"tol": 1e-3, "forms_64rhs": forms, "warm_start_512rhs": warm,
+            "note": "ms = launch (or pipeline) time until the last right-hand side stops, median of 3; "
+                    "time_vs_plain_f32 < 1 is a gain"}
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -800,28 +930,11 @@ def run_native(args):
     wl.setup(ss, dev, rank)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    for _ in range(args.warmup):
-        wl.step(ss, wl.p, wl.f, ss.LAYOUT_IMAGE)
-    torch.cuda.synchronize()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    s_solve = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if ws > 1:
         dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            starts[k].record(stream)
-            wl.step(ss, wl.p, wl.f, ss.LAYOUT_IMAGE, s_solve[k])
-            ends[k].record(stream)
-        torch.cuda.synchronize()
+    step_ms, solve_ms, clocks, units = time_steps(wl, ss, args.steps, args.warmup, stream, flush, local)
     if ws > 1:
         dist.barrier()
-    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    solve_ms = sum(a.elapsed_time(b) for a, b in s_solve) / args.steps
-    units = wl.units(ss)
 
     # End to end through the public API with host buffers: pinned p in, image out.
     p_host = wl.p.cpu().pin_memory()
@@ -867,17 +980,27 @@ def run_native(args):
         "data": "synthetic (seeded random ellipses, Siddon projections)",
         "config": wl.config(),
         "e2e": {"value": e2e_value, "unit": wl.unit, "h2d_bytes_per_step": wl.p.numel() * 4,
-                "d2h_bytes_per_step": wl.f.numel() * 4},
+                "d2h_bytes_per_step": wl.f.numel() * 4,
+                "path": "the Python binding over the C ABI; the host<->device copies are torch's pinned-memory "
+                        "copies, outside the library (its entry points take device pointers)"},
         "gpu_launches": wl.launches * args.steps,
         "roofline": wl.roofline(ss, solve_ms),
-        "clocks": clocks.summary(),
+        "clocks": clocks,
         "breakdown_ms": {"solve": solve_ms, "fold_A": fold_ms, "step": step_ms / args.steps},
     }
     out.update(extra)
+    if args.workload == "realistic" and not args.no_extras:
+        # The metric's other two clauses, on the same GPU in the same run: the HBM roofline
+        # on the batch (whose inputs far exceed L2) and the time to rho <= 1e-3 of each form.
+        del wl
+        torch.cuda.empty_cache()
+        out["batch"] = batch_record(ss, dev, rank, stream, flush, local, args.batch_steps, 3)
+        out["time_to_tol"] = time_to_tol_record(ss, dev, rank, stream)
     if rank == 0 and not args.no_cpu_baseline:
-        _, out["cpu_baseline"] = oracle_throughput(wl, args.cpu_seconds)
-        if wl.two_process_baseline:
-            out["cpu_baseline_2proc"] = oracle_two_process(wl, out["cpu_baseline"]["value"], args.cpu_seconds)
+        wl0 = WORKLOADS[args.workload]()
+        _, out["cpu_baseline"] = oracle_throughput(wl0, args.cpu_seconds)
+        if wl0.two_process_baseline:
+            out["cpu_baseline_2proc"] = oracle_two_process(wl0, out["cpu_baseline"]["value"], args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
@@ -926,6 +1049,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--slices", type=int, default=256, help="batch workload: number of slices (first n of the 256)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="realistic workload: skip the batch record and the time-to-tolerance record")
+    ap.add_argument("--batch-steps", type=int, default=5, help="timed steps of the batch record")
     args = ap.parse_args()
     Batch.n_slices = max(1, min(256, args.slices))
     if args.steps is None:
