@@ -352,6 +352,75 @@ typedef struct splitsart_solve_info {
 int splitsart_solve_result(splitsart_system* sys, splitsart_solve_info* info);
 
 /*
+ * Options of splitsart_solve_os. Zero-initialise, then set fields.
+ */
+typedef struct splitsart_os_opts {
+    int32_t subset_rows; /* folded rows per subset; 0 = one folded view pair (the geometry's nb rows) */
+    int32_t cone;        /* 1: keep every voxel of the image non-negative (f2 >= |f1|) */
+    int32_t reserved[2]; /* zero */
+} splitsart_os_opts;
+
+/*
+ * Ordered-subsets SART (OS-SART) on both split systems, with an optional
+ * non-negativity constraint, in one persistent cooperative launch.
+ *
+ * SART as Andersen and Kak state it (Section 1, reference [001]) updates the
+ * image once per projection view. Here the folded rows are taken in subsets
+ * of subset_rows consecutive rows; by default a subset is one folded view
+ * pair (rows t nb .. t nb + nb - 1 carry the rays of sources t and K-1-t).
+ * One iteration applies, for t = 0, 1, ..., T-1 in turn and each system s:
+ *     u_i = (p^s_i - (A_s f)_i) / R_i                     for rows i of subset t
+ *     f_j += lambda (sum_{i in subset t} a_ij u_i) / C_t,j
+ * with C_t,j = sum_{i in subset t} |a_ij| and 1/0 := 0. With one subset this
+ * is splitsart_solve's simultaneous SART.
+ *
+ * The cone: f >= 0 for the image holds iff f2_j >= |f1_j| for every voxel
+ * pair (Eq. 5). With cone = 1 the start and every subset update are
+ * projected onto it: recombine the pair, clip both voxels at zero, fold
+ * again.
+ *
+ * Stopping: rho_k = ||A f^k - p|| / ||p|| of the iterate after k full
+ * sweeps, tested when k is a multiple of opts->check_every or k =
+ * opts->max_iters, before the sweep. With more than one subset a test costs
+ * one extra forward pass. The result is read by splitsart_solve_result.
+ *
+ * opts: max_iters, lambda, tol, check_every, block_threads (at most 512),
+ * lanes_per_col, timeout_ms and inject_barrier_fault are used; the other
+ * fields are ignored.
+ * The first call for a subset size builds per-subset column tables on the
+ * device (about 12 bytes per subset and non-empty column) and keeps them
+ * with the system.
+ * Errors: SPLITSART_ERR_ARG for a batch system, a BF16/FP16 system, or
+ * subset_rows = 0 on a system folded from a CSR (no geometry).
+ */
+int splitsart_solve_os(splitsart_system* sys, const void* p12_dev, void* f12_dev, const splitsart_solve_opts* opts,
+                       const splitsart_os_opts* os, void* stream);
+
+/*
+ * CGLS on both split systems in one persistent cooperative launch.
+ *
+ * The normal matrix of each split system is the fold of the full normal
+ * matrix (text after Eq. 18): B_s = A_s^T A_s. CGLS runs conjugate gradients
+ * on A_s^T A_s f = A_s^T p_s without forming B_s: one pass over the folded
+ * CSR (q = A d) and one over the folded CSC (s = A^T r) per iteration, both
+ * systems in the same passes, each with its own step lengths. From f^0 = 0 on
+ * a consistent system the iterates tend to the normal pseudo-solution, so the
+ * recombined image tends to the full system's (Theorem 2).
+ *
+ * Stopping is the joint rule of splitsart_solve: rho_k = ||A f^k - p|| / ||p||
+ * tested before step k when k is a multiple of opts->check_every or k =
+ * opts->max_iters. Reductions are FP64 in a fixed order; repeated runs of one
+ * launch shape are bitwise identical.
+ * opts: max_iters, tol, check_every, block_threads (at most 512),
+ * lanes_per_col, timeout_ms and inject_barrier_fault are used (lambda is not).
+ * The first call allocates four work vectors (2 Mh + 2 Nh pairs), kept with
+ * the system. The result is read by splitsart_solve_result.
+ * Errors: SPLITSART_ERR_ARG for a batch system or a BF16/FP16 system.
+ */
+int splitsart_solve_cgls(splitsart_system* sys, const void* p12_dev, void* f12_dev, const splitsart_solve_opts* opts,
+                         void* stream);
+
+/*
  * Allocation-free solve. The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc. Examples are a process that
  * reserves all of its device memory at start-up and forbids allocation

@@ -205,6 +205,7 @@ int create_system(const splitsart_geometry* const* geoms, int ns, int dtype, cud
     if (ns == 1) {
         s->nx = nxs[0];
         s->nz = nzs[0];
+        if (geoms[0]->has_params) s->nb = geoms[0]->params.nb;
     }
     const size_t pb = pair_bytes(dtype), nb = norm_pair_bytes(dtype), vb = vec_pair_bytes(dtype);
     const int64_t mx = (Mh > Nh ? Mh : Nh) + 1;
@@ -344,9 +345,11 @@ extern "C" int splitsart_refold(splitsart_system* s, void* stream) {
 
 extern "C" void splitsart_system_destroy(splitsart_system* s) {
     if (!s) return;
-    if (s->base || s->res_alloc) cudaStreamSynchronize(s->last);
+    if (s->base || s->res_alloc || s->os_alloc || s->cg_alloc) cudaStreamSynchronize(s->last);
     if (s->base) cudaFree(s->base);
     if (s->res_alloc) cudaFree(s->res_alloc);
+    if (s->os_alloc) cudaFree(s->os_alloc);
+    if (s->cg_alloc) cudaFree(s->cg_alloc);
     delete s;
 }
 
@@ -483,6 +486,35 @@ extern "C" int splitsart_solve(splitsart_system* s, const void* p12, void* f12, 
     if (!(o->timeout_ms >= 0.0)) return fail(SPLITSART_ERR_ARG, "solve: timeout_ms must be >= 0");
     s->last = (cudaStream_t)stream;
     return run_solve(s, p12, f12, *o, (cudaStream_t)stream);
+}
+
+extern "C" int splitsart_solve_os(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts* o,
+                                  const splitsart_os_opts* os, void* stream) {
+    splitsart::NvtxRange nvtx_range("splitsart_solve_os");
+    if (!s || !o || !os) return fail(SPLITSART_ERR_ARG, "solve_os: NULL argument");
+    if ((s->Mh > 0 && !p12) || (s->Nh > 0 && !f12)) return fail(SPLITSART_ERR_ARG, "solve_os: NULL vector");
+    if (o->max_iters < 0 || o->max_iters > 500000)
+        return fail(SPLITSART_ERR_ARG, "solve_os: max_iters must be in [0, 500000]");
+    if (!(o->lambda > 0.0) || !std::isfinite(o->lambda)) return fail(SPLITSART_ERR_ARG, "solve_os: lambda must be > 0");
+    if (!(o->tol >= 0.0)) return fail(SPLITSART_ERR_ARG, "solve_os: tol must be >= 0");
+    if (o->check_every < 0) return fail(SPLITSART_ERR_ARG, "solve_os: check_every must be >= 0");
+    if (!(o->timeout_ms >= 0.0)) return fail(SPLITSART_ERR_ARG, "solve_os: timeout_ms must be >= 0");
+    s->last = (cudaStream_t)stream;
+    return run_solve_os(s, p12, f12, *o, *os, (cudaStream_t)stream);
+}
+
+extern "C" int splitsart_solve_cgls(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts* o,
+                                    void* stream) {
+    splitsart::NvtxRange nvtx_range("splitsart_solve_cgls");
+    if (!s || !o) return fail(SPLITSART_ERR_ARG, "solve_cgls: NULL argument");
+    if ((s->Mh > 0 && !p12) || (s->Nh > 0 && !f12)) return fail(SPLITSART_ERR_ARG, "solve_cgls: NULL vector");
+    if (o->max_iters < 0 || o->max_iters > 500000)
+        return fail(SPLITSART_ERR_ARG, "solve_cgls: max_iters must be in [0, 500000]");
+    if (!(o->tol >= 0.0)) return fail(SPLITSART_ERR_ARG, "solve_cgls: tol must be >= 0");
+    if (o->check_every < 0) return fail(SPLITSART_ERR_ARG, "solve_cgls: check_every must be >= 0");
+    if (!(o->timeout_ms >= 0.0)) return fail(SPLITSART_ERR_ARG, "solve_cgls: timeout_ms must be >= 0");
+    s->last = (cudaStream_t)stream;
+    return run_solve_cgls(s, p12, f12, *o, (cudaStream_t)stream);
 }
 
 extern "C" int splitsart_solve_result(splitsart_system* s, splitsart_solve_info* info) {

@@ -135,6 +135,23 @@ struct splitsart_system {
     int32_t* res_loc = nullptr;    // [n_nzr + G] per group: local entry offsets of its rows, then its total
     long long res_row_bytes = 0;   // the largest CTA's shared-memory bytes for its rows
     void* res_alloc = nullptr;     // device allocation of the plan
+
+    // Detector bins of a single-slice system folded from acquisition parameters
+    // (0 otherwise): the rows of one folded view pair.
+    int nb = 0;
+
+    // Ordered-subsets tables (os_sart.cu), built on the first ordered-subsets
+    // solve for a subset size and kept: a refold rebuilds the same pattern and
+    // values from the same uploaded half rows.
+    int os_rows = 0;                // folded rows per subset of the tables below (0: none yet)
+    int os_T = 0;                   // subsets
+    int32_t* os_qr = nullptr;       // [T + 1] compacted-row range of each subset
+    int32_t* os_off = nullptr;      // [(T + 1) x n_nzc] start of each subset's entries in each compacted column
+    void* os_invC = nullptr;        // [T x n_nzc] pairs 1/C_t (vector type), 0 where C_t = 0
+    void* os_alloc = nullptr;       // device allocation of the tables
+
+    // Conjugate-gradient work vectors (cgls.cu), allocated on the first CGLS solve.
+    void* cg_alloc = nullptr;
 };
 
 namespace splitsart {
@@ -152,4 +169,8 @@ int run_solve(splitsart_system* s, const void* p12, void* f12, const splitsart_s
 int cuda_fail(cudaError_t e, const char* what);
 // Defined in api.cu: the fold statistics on the host (one synchronisation on first use).
 int system_host_stats(splitsart_system* s, FoldStats* out);
+// Defined in os_sart.cu and cgls.cu.
+int run_solve_os(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o,
+                 const splitsart_os_opts& os, cudaStream_t st);
+int run_solve_cgls(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o, cudaStream_t st);
 }  // namespace splitsart

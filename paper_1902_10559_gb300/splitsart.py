@@ -48,6 +48,10 @@ class SolveOpts(ctypes.Structure):
                 ("row_weight", ctypes.c_int32)]
 
 
+class OsOpts(ctypes.Structure):
+    _fields_ = [("subset_rows", ctypes.c_int32), ("cone", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("rho", ctypes.c_double),
                 ("rr", ctypes.c_double), ("pp", ctypes.c_double)]
@@ -88,6 +92,8 @@ _SIGS = {
     "splitsart_project": ([_P, _P, ctypes.c_int, _P, _P], ctypes.c_int),
     "splitsart_solve": ([_P, _P, _P, ctypes.POINTER(SolveOpts), _P], ctypes.c_int),
     "splitsart_solve_result": ([_P, ctypes.POINTER(SolveInfo)], ctypes.c_int),
+    "splitsart_solve_os": ([_P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(OsOpts), _P], ctypes.c_int),
+    "splitsart_solve_cgls": ([_P, _P, _P, ctypes.POINTER(SolveOpts), _P], ctypes.c_int),
     "splitsart_solve_static": ([ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                 ctypes.POINTER(SolveOpts), _P, _P], ctypes.c_int),
     "splitsart_cnn_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
@@ -340,6 +346,27 @@ def solve(system: System, p12, f12, opts: SolveOpts, stream=None) -> None:
     vt = system.vec_dtype
     _check(lib().splitsart_solve(system.handle, _dev_ptr(p12, 2 * system.Mh, vt, "p12"),
                                  _dev_ptr(f12, 2 * system.Nh, vt, "f12"), ctypes.byref(opts), _stream_ptr(stream)))
+
+
+def solve_os(system: System, p12, f12, opts: SolveOpts, subset_rows: int = 0, cone: bool = False,
+             stream=None) -> None:
+    """Enqueue ordered-subsets SART (splitsart_solve_os); read the result with solve_result.
+
+    subset_rows = 0 takes one folded view pair per subset. cone keeps the image non-negative.
+    """
+    vt = system.vec_dtype
+    os_opts = OsOpts(int(subset_rows), int(bool(cone)))
+    _check(lib().splitsart_solve_os(system.handle, _dev_ptr(p12, 2 * system.Mh, vt, "p12"),
+                                    _dev_ptr(f12, 2 * system.Nh, vt, "f12"), ctypes.byref(opts),
+                                    ctypes.byref(os_opts), _stream_ptr(stream)))
+
+
+def solve_cgls(system: System, p12, f12, opts: SolveOpts, stream=None) -> None:
+    """Enqueue CGLS on both split systems (splitsart_solve_cgls); read the result with solve_result."""
+    vt = system.vec_dtype
+    _check(lib().splitsart_solve_cgls(system.handle, _dev_ptr(p12, 2 * system.Mh, vt, "p12"),
+                                      _dev_ptr(f12, 2 * system.Nh, vt, "f12"), ctypes.byref(opts),
+                                      _stream_ptr(stream)))
 
 
 def solve_result(system: System, raise_on_error: bool = True) -> dict:
