@@ -50,6 +50,7 @@ extern "C" {
 #define SPLITSART_ERR_NOMEM (-6)      /* device or host allocation failed */
 #define SPLITSART_ERR_STATE (-7)      /* call made in the wrong order */
 #define SPLITSART_ERR_NONFINITE (-8)  /* the input holds NaN or Inf */
+#define SPLITSART_ERR_NOT_SPD (-9)    /* a normal matrix is not positive definite: the matrix lacks full column rank */
 
 /* ---- value storage of the folded matrices ---- */
 #define SPLITSART_F64 0  /* double pairs, double vectors and normalisers */
@@ -297,8 +298,16 @@ typedef struct splitsart_solve_opts {
     int32_t kernel;        /* 0 = choose (2 if the system fits on chip, else 3); 1 = stream the matrix in
                               CTA-wide tiles; 2 = keep it in shared memory; 3 = stream it row by row
                               through registers; 4 = stream it per warp through shared memory with
-                              bulk asynchronous copies (lanes_per_col 4 or 8 only). 3 and 4 have no
-                              CTA barriers inside a pass */
+                              bulk asynchronous copies (lanes_per_col 4 or 8 only); 5 = stream it row by
+                              row in compacted index order, each warp loading its next chunk's row and
+                              column data ahead;
+                              6 = kernel 5 on the implicit fold (each half-row entry of A stored once,
+                              its folded column carrying A1's sign: 8 instead of 12 bytes per entry and
+                              pass in FP32; results differ from the explicit fold by rounding where a
+                              ray and its mirror cross the same folded cell). 3 to 6 have no CTA
+                              barriers inside a pass. 5 and 6: FP64 and FP32 systems, lanes_per_col 4
+                              or 8; their first use builds the re-indexed copy of the matrix (4 bytes
+                              per entry and pass for 5, 8 or 12 for 6) and keeps it with the system */
     double timeout_ms;     /* limit of each grid-barrier wait; 0 = default (2000 ms) */
     int32_t inject_barrier_fault; /* test hook: the barrier also waits for a CTA that never comes */
     int32_t tile_entries;  /* streaming kernel: entries staged per tile, 0 = default; multiple of 1024 in [1024, 16384] */
@@ -419,6 +428,52 @@ int splitsart_solve_os(splitsart_system* sys, const void* p12_dev, void* f12_dev
  */
 int splitsart_solve_cgls(splitsart_system* sys, const void* p12_dev, void* f12_dev, const splitsart_solve_opts* opts,
                          void* stream);
+
+/*
+ * ---- The direct method (Example 2, Table 1) ----
+ * Least squares A x = b through the normal equations, dense, in FP64 on the
+ * device: B = A^T A and c = A^T b from the CSR and CSC of A (row j of B is
+ * accumulated in one CTA's shared memory, in a fixed order), a blocked
+ * Cholesky factorisation B = L L^T (blocks of 64), then L y = c and
+ * L^T x = y. The split form applies it to A1 and A2, whose normal matrices
+ * are the folds of A^T A (text after Eq. 18), and recombines by Theorem 1.
+ *
+ * splitsart_normal_solve_bytes: bytes of the work buffer for n unknowns
+ * (8 n^2 + 8 n + 256).
+ */
+int splitsart_normal_solve_bytes(int64_t n, int64_t* bytes);
+
+/*
+ * The normal-equation solve of any m x n matrix with full column rank.
+ * - CSR: rp_dev[m+1], col_dev (columns increasing within a row), val_dev;
+ *   CSC: cp_dev[n+1], row_dev (rows increasing within a column), valT_dev.
+ *   Values are doubles read at stride val_stride: 1 for plain arrays, 2 for
+ *   one member of an interleaved pair array (pointer offset by 0 or 1).
+ * - b_dev[m] at stride b_stride; x_dev[n] (output) at stride x_stride.
+ * - work_dev: caller-owned device buffer of splitsart_normal_solve_bytes(n).
+ * - status_dev: device int32, written 0, or SPLITSART_ERR_NOT_SPD when a
+ *   pivot of the factorisation is not positive (the later steps are skipped
+ *   and x_dev is not written). A column without entries (a voxel no ray
+ *   crosses) gives a zero pivot. A matrix that is singular only numerically
+ *   may leave a tiny positive pivot instead: full column rank is the
+ *   caller's to ensure.
+ * n is limited by one CTA's shared memory (8 bytes per unknown; about 29000
+ * on this GPU). Errors found before the launch are returned directly.
+ */
+int splitsart_normal_solve(int64_t m, int64_t n, const int32_t* rp_dev, const int32_t* col_dev, const double* val_dev,
+                           const int32_t* cp_dev, const int32_t* row_dev, const double* valT_dev, int32_t val_stride,
+                           const double* b_dev, int32_t b_stride, double* x_dev, int32_t x_stride, void* work_dev,
+                           int32_t* status_dev, void* stream);
+
+/*
+ * The split direct method on a folded FP64 single-slice system: fold p (after
+ * Eq. 4), the normal-equation solves of A1 and of A2 one after the other (they
+ * share work_dev, splitsart_normal_solve_bytes(N/2) bytes), and the Theorem 1
+ * recombination into f_dev[N] (snake order). p_dev[M] FP64. status_dev as for
+ * splitsart_normal_solve.
+ */
+int splitsart_direct_split(splitsart_system* sys, const double* p_dev, double* f_dev, void* work_dev,
+                           int32_t* status_dev, void* stream);
 
 /*
  * Allocation-free solve. The paper has no counterpart: this entry point

@@ -5,8 +5,9 @@ cached per (device, storage type, problem class) in a JSON file:
 $SPLITSART_TUNE_CACHE, or ~/.cache/splitsart/tune.json.
 
 - Persistent solve: kernel (shared-memory resident, tile streaming, row
-  streaming through registers, or per-warp bulk-staged streaming), tile entries per CTA, lanes per column in the back-projection,
-  threads per CTA.
+  streaming through registers, row streaming in compacted index order, or
+  per-warp bulk-staged streaming), tile entries per CTA, lanes per column in
+  the back-projection, threads per CTA.
 - Multi-right-hand-side solve: right-hand sides per CTA, threads per CTA.
 
 The tuner only chooses among launch shapes of the same arithmetic, so every
@@ -86,8 +87,10 @@ def solve_candidates(system: ss.System) -> list[dict]:
                 for rw in (0, 160, 320):  # rows' fixed weight in the CTA row plan (0 = library default)
                     out.append({"kernel": 2, "lanes_per_col": lpc, "block_threads": bt, "tile_entries": 0,
                                 "row_weight": rw})
-    for kern, bts in ((4, (256, 384)), (3, (256, 512))):
-        for lpc in ((4, 8) if kern == 4 else (4, 8, 16)):
+    for kern, bts in ((4, (256, 384)), (3, (256, 512)), (5, (256, 512))):
+        if kern == 5 and system.dtype not in (ss.F64, ss.F32):
+            continue  # the compacted streaming kernel takes FP64 and FP32 systems
+        for lpc in ((4, 8) if kern in (4, 5) else (4, 8, 16)):
             for bt in bts:
                 out.append({"kernel": kern, "lanes_per_col": lpc, "block_threads": bt, "tile_entries": 0})
     for lpc in (4, 8, 16):

@@ -651,6 +651,71 @@ int project_typed(splitsart_system* s, const void* f, int layout, void* p, cudaS
 
 }  // namespace
 
+namespace {
+
+// The implicit fold of the half rows: folded row i lists every entry of half
+// row i once, in the merged column order of the fold (L before its R' twin on
+// equal columns), as (global folded column with A1's sign in bit 31, w). The
+// entry at merged position d goes to hrp[i] + d. One warp per row.
+template <class V>
+__global__ void __launch_bounds__(kFoldWarps * 32) implicit_rows_kernel(int64_t Mh, SliceMap sm,
+                                                                        const int64_t* __restrict__ hrp,
+                                                                        const int32_t* __restrict__ hcol,
+                                                                        const double* __restrict__ hval,
+                                                                        int32_t* __restrict__ out_col,
+                                                                        V* __restrict__ out_val) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = blockIdx.x * (int64_t)kFoldWarps + w;
+    if (i >= Mh) return;
+    double* sv = reinterpret_cast<double*>(smem) + (size_t)w * kRowCap;
+    int32_t* sc = reinterpret_cast<int32_t*>(smem + (size_t)kFoldWarps * kRowCap * 8) + (size_t)w * kRowCap;
+    const int s = slice_of(sm.rows, sm.ns, i);
+    const HalfRow h = stage_half_row(hrp, hcol, hval, i, (int)(sm.N[s + 1] - sm.N[s]), sc, sv, lane);
+    const long long col0 = sm.cols[s];
+    const int64_t e0 = hrp[i];
+    const int d0 = (int)((long long)lane * h.n / 32), d1 = (int)((long long)(lane + 1) * h.n / 32);
+    const int nR = h.n - h.nL;
+    int a = merge_split(h, d0), b = d0 - a;
+    for (int d = d0; d < d1; ++d) {
+        if (a < h.nL && (b >= nR || h.Lc(a) <= h.Rc(b))) {
+            out_col[e0 + d] = (int32_t)(col0 + h.Lc(a));
+            out_val[e0 + d] = (V)h.Lv(a);
+            ++a;
+        } else {
+            out_col[e0 + d] = (int32_t)((uint32_t)(col0 + h.Rc(b)) | 0x80000000u);
+            out_val[e0 + d] = (V)h.Rv(b);
+            ++b;
+        }
+    }
+}
+
+}  // namespace
+
+int run_implicit_rows(const splitsart_system* s, bool fp64, int32_t* col, void* val, cudaStream_t st) {
+    if (s->Mh <= 0) return SPLITSART_OK;
+    const size_t row_smem = (size_t)kFoldWarps * kRowCap * (8 + 4);
+    const unsigned row_blocks = (unsigned)((s->Mh + kFoldWarps - 1) / kFoldWarps);
+    const SliceMap sm = slice_map(s);
+    if (fp64) {
+        cudaFuncSetAttribute((const void*)implicit_rows_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)row_smem);
+        implicit_rows_kernel<double><<<row_blocks, kFoldWarps * 32, row_smem, st>>>(s->Mh, sm, s->hrp, s->hcol,
+                                                                                   s->hval, col, (double*)val);
+    } else {
+        cudaFuncSetAttribute((const void*)implicit_rows_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)row_smem);
+        implicit_rows_kernel<float><<<row_blocks, kFoldWarps * 32, row_smem, st>>>(s->Mh, sm, s->hrp, s->hcol,
+                                                                                  s->hval, col, (float*)val);
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SPLITSART_OK : cuda_fail(e, "implicit fold: rows");
+}
+
+int scan_exclusive(const int32_t* in, int32_t* out, int32_t* tile_sums, int64_t n, cudaStream_t st) {
+    return exclusive_scan(in, out, tile_sums, n, st);
+}
+
 int run_fold(splitsart_system* s, cudaStream_t st) {
     switch (s->dtype) {
         case SPLITSART_F64: return fold_typed<TF64>(s, st);

@@ -50,6 +50,35 @@ struct SliceMap {
     const int* nz;          // [ns]
 };
 
+// A folded system re-indexed for the pipelined streaming solve (stream.cu):
+// rows and columns are renumbered in compacted order (only those with
+// entries), so the hot loop never looks an index up. Two storages:
+// - explicit: the folded CSR/CSC pairs (a1, a2) themselves, 12 bytes per entry
+//   per pass in FP32;
+// - implicit: each entry of the half rows of A stored once, as the compacted
+//   folded column (row) with A1's sign in bit 31 and its one length w:
+//   a1 = +-w, a2 = w, 8 bytes per entry per pass in FP32. A ray and its mirror
+//   through the same folded cell give two entries (+w, then -w').
+struct StreamFmt {
+    int built = 0;
+    void* alloc = nullptr;
+    int32_t* rp = nullptr;   // [n_nzr + 1] compacted-row pointers
+    int32_t* ci = nullptr;   // CSR indices: compacted columns (implicit: A1's sign in bit 31)
+    const void* cv = nullptr;  // CSR values: pairs (explicit) or single values (implicit)
+    int32_t* cp = nullptr;   // [n_nzc + 1] compacted-column pointers
+    int32_t* ri = nullptr;   // CSC indices: compacted rows (implicit: A1's sign in bit 31)
+    const void* rv = nullptr;  // CSC values
+    void* ir = nullptr;      // [n_nzr] 1/R as applied, compacted
+    void* ic = nullptr;      // [n_nzc] 1/C as applied, compacted
+    void* pc = nullptr;      // [n_nzr] pairs: p of the launch, compacted
+    void* uc = nullptr;      // [n_nzr] pairs: u
+    void* fc = nullptr;      // [n_nzc] pairs: f of the launch, compacted
+    double* rr = nullptr;    // [n_nzr] per-row residual^2 (batch stop tests)
+    int32_t* qs = nullptr;   // [ns + 1] first compacted row of each slice
+    int32_t* cs = nullptr;   // [n_nzc] slice of each compacted column
+    double* pz = nullptr;    // [ns] ||p||^2 of each slice's empty rows (per launch)
+};
+
 // Per-slice solve state of a batch launch.
 struct SliceSolve {
     int iters;
@@ -152,6 +181,10 @@ struct splitsart_system {
 
     // Conjugate-gradient work vectors (cgls.cu), allocated on the first CGLS solve.
     void* cg_alloc = nullptr;
+
+    // Compacted streaming formats (stream.cu): [0] explicit, [1] implicit,
+    // each built on its first use and kept.
+    splitsart::StreamFmt st[2];
 };
 
 namespace splitsart {
@@ -173,4 +206,12 @@ int system_host_stats(splitsart_system* s, FoldStats* out);
 int run_solve_os(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o,
                  const splitsart_os_opts& os, cudaStream_t st);
 int run_solve_cgls(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o, cudaStream_t st);
+int run_solve_stream(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o, cudaStream_t st);
+// Defined in fold.cu: the implicit fold of the half rows (entry d of half row i
+// at hrp[i] + d, in the fold's merged column order), as global folded columns
+// with A1's sign in bit 31 and FP64 or FP32 lengths.
+int run_implicit_rows(const splitsart_system* s, bool fp64, int32_t* col, void* val, cudaStream_t st);
+// Defined in fold.cu: exclusive scan of in[0..n) into out[0..n] (out[n] = total);
+// tile_sums holds n / 4096 + 2 ints.
+int scan_exclusive(const int32_t* in, int32_t* out, int32_t* tile_sums, int64_t n, cudaStream_t st);
 }  // namespace splitsart

@@ -22,7 +22,8 @@ LAYOUT_SNAKE, LAYOUT_IMAGE = 0, 1
 DTYPE_NAMES = {"f64": F64, "f32": F32, "bf16": BF16, "f16": F16}
 
 OK = 0
-ERR_ARG, ERR_ODD_DIM, ERR_ASYMMETRIC, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_STATE, ERR_NONFINITE = range(-1, -9, -1)
+ERR_ARG, ERR_ODD_DIM, ERR_ASYMMETRIC, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_STATE, ERR_NONFINITE, ERR_NOT_SPD = range(
+    -1, -10, -1)
 
 
 class GeometryParams(ctypes.Structure):
@@ -94,6 +95,10 @@ _SIGS = {
     "splitsart_solve_result": ([_P, ctypes.POINTER(SolveInfo)], ctypes.c_int),
     "splitsart_solve_os": ([_P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(OsOpts), _P], ctypes.c_int),
     "splitsart_solve_cgls": ([_P, _P, _P, ctypes.POINTER(SolveOpts), _P], ctypes.c_int),
+    "splitsart_normal_solve_bytes": ([ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "splitsart_normal_solve": ([ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P, _P, ctypes.c_int32, _P,
+                                ctypes.c_int32, _P, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
+    "splitsart_direct_split": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
     "splitsart_solve_static": ([ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                 ctypes.POINTER(SolveOpts), _P, _P], ctypes.c_int),
     "splitsart_cnn_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
@@ -367,6 +372,63 @@ def solve_cgls(system: System, p12, f12, opts: SolveOpts, stream=None) -> None:
     _check(lib().splitsart_solve_cgls(system.handle, _dev_ptr(p12, 2 * system.Mh, vt, "p12"),
                                       _dev_ptr(f12, 2 * system.Nh, vt, "f12"), ctypes.byref(opts),
                                       _stream_ptr(stream)))
+
+
+def normal_solve_bytes(n: int) -> int:
+    out = ctypes.c_int64()
+    _check(lib().splitsart_normal_solve_bytes(int(n), ctypes.byref(out)))
+    return out.value
+
+
+class DenseSolver:
+    """Device work buffer and status word of the direct method (splitsart_normal_solve / splitsart_direct_split)."""
+
+    def __init__(self, n: int, device="cuda"):
+        import torch
+        self.n = int(n)
+        self.work = torch.empty(normal_solve_bytes(n), dtype=torch.uint8, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def result(self) -> int:
+        """Synchronise and return the status word: OK or ERR_NOT_SPD."""
+        return int(self.status.item())
+
+
+def normal_solve(solver: DenseSolver, m: int, n: int, csr, csc, b, x, val_stride: int = 1, b_stride: int = 1,
+                 x_stride: int = 1, stream=None) -> None:
+    """Enqueue the normal-equation solve of an m x n matrix given as device (rp, col, val) CSR and (cp, row, valT) CSC."""
+    rp, col, val = csr
+    cp, row, valT = csc
+    _check(lib().splitsart_normal_solve(int(m), int(n), rp.data_ptr(), col.data_ptr(), val.data_ptr(), cp.data_ptr(),
+                                        row.data_ptr(), valT.data_ptr(), val_stride, b.data_ptr(), b_stride,
+                                        x.data_ptr(), x_stride, solver.work.data_ptr(), solver.status.data_ptr(),
+                                        _stream_ptr(stream)))
+
+
+def direct_split(system: System, solver: DenseSolver, p, f, stream=None) -> None:
+    """Enqueue the split direct method on an FP64 system: p[M] in, f[N] (snake order) out."""
+    _check(lib().splitsart_direct_split(system.handle, _dev_ptr(p, system.M, system.vec_dtype, "p"),
+                                        _dev_ptr(f, system.N, system.vec_dtype, "f"), solver.work.data_ptr(),
+                                        solver.status.data_ptr(), _stream_ptr(stream)))
+
+
+def full_csr(geometry: Geometry):
+    """Host CSR (row_ptr, col, val) of the full M x N matrix, from the stored half rows and Eq. (2).
+
+    Row M-1-i is the reflection of row i: w_{M-1-i, N-1-j} = w_{i,j}.
+    """
+    rp, col, val = geometry.export()
+    M, N, Mh = geometry.M, geometry.N, geometry.M // 2
+    lens = np.diff(rp)
+    full_rp = np.zeros(M + 1, dtype=np.int64)
+    full_rp[1:Mh + 1] = np.cumsum(lens)
+    full_rp[Mh + 1:] = full_rp[Mh] + np.cumsum(lens[::-1])
+    cols = [col]
+    vals = [val]
+    for i in range(Mh - 1, -1, -1):  # rows Mh .. M-1 mirror rows Mh-1 .. 0
+        cols.append((N - 1 - col[rp[i]:rp[i + 1]])[::-1])
+        vals.append(val[rp[i]:rp[i + 1]][::-1])
+    return full_rp, np.concatenate(cols).astype(np.int32), np.concatenate(vals)
 
 
 def solve_result(system: System, raise_on_error: bool = True) -> dict:
