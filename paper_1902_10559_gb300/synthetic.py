@@ -144,6 +144,26 @@ def covering_detector_width(nx: int, nz: int, W: float, H: float, z0: float, K: 
     return 2.0 * far * margin
 
 
+def table1_geometries() -> list:
+    """The three sizes of Example 2 (Table 1): 32x32, 64x64 and 128x128 voxels with 24, 48 and 96 positions.
+
+    Table 1 prints A's sizes as 1024 x 2280, 4096 x 9120 and 16384 x 36480
+    (N x M), so each source has M / K = 95, 190 and 380 detector bins. The other
+    parameters are not in the paper. A 128 mm square object (voxels of 4, 2
+    and 1 mm) 50 mm above the detector, sources on a +/-20 deg arc at 600 mm
+    and a detector covering the object's shadow give systems of full column
+    rank (condition numbers of A about 4e3, 2e4 and 6e4); a 256 mm object at
+    128 x 128 does not (its detector, 1068 mm wide, has bins coarser than the
+    voxels).
+    """
+    out = []
+    for n, K, nb in ((32, 24, 95), (64, 48, 190), (128, 96, 380)):
+        W = H = 128.0
+        D = covering_detector_width(n, n, W, H, 50.0, K, 20.0, 600.0)
+        out.append(Geometry(nx=n, nz=n, W=W, H=H, z0=50.0, K=K, gamma_deg=20.0, R=600.0, nb=nb, D=D))
+    return out
+
+
 def batch_geometries(n_slices: int = 256, seed: int = 3, nx_choices=(256, 512, 768, 1024), nz_range=(64, 256),
                      K_range=(16, 32)) -> list:
     """Draw a batch of uneven slices with seeded sizes.
