@@ -150,7 +150,7 @@ def profile_traffic(name: str, src: str = KERNEL_SRC, algorithmic_bytes: float |
     return None
 
 
-def algorithmic_bytes_per_launch(S, Mh, Nh, iters, batch_rows=0):
+def algorithmic_bytes_per_launch(S, Mh, Nh, iters, batch_rows=0, bytes_per_entry=12):
     """Algorithmic bytes of one persistent FP32 solve.
 
     Forward pass (iters + 1 of them):
@@ -165,9 +165,11 @@ def algorithmic_bytes_per_launch(S, Mh, Nh, iters, batch_rows=0):
       24 Nh          f pair read and write, 1/C pair read
     A batch adds, per forward pass, 16 B per row: the per-row residual written
     and read back by its slice's stop test.
+    The implicit fold stores each half-row entry once (4 B index with the sign,
+    4 B length): bytes_per_entry = 8 with S = the half rows' entries.
     """
-    fwd = 12 * S + 4 * (Mh + 1) + 24 * Mh + 8 * Nh + 16 * batch_rows
-    bwd = 12 * S + 4 * (Nh + 1) + 8 * Mh + 24 * Nh
+    fwd = bytes_per_entry * S + 4 * (Mh + 1) + 24 * Mh + 8 * Nh + 16 * batch_rows
+    bwd = bytes_per_entry * S + 4 * (Nh + 1) + 8 * Mh + 24 * Nh
     return (iters + 1) * fwd + iters * bwd
 
 
@@ -408,11 +410,66 @@ class Batch(Realistic):
             del host, sysm
         return {"forms": self.form_times(ss, self.geoms), "geometry_s": self.geometry_s}
 
+    def form_times(self, ss, geoms):
+        """Solve time of the same inputs in each storage form and kernel, each with its own roofline.
+
+        f32: the timed solve (autotuned launch shape). f32_rows: the row-streaming
+        kernel (3). f32_compact: the compacted-order kernel (5) on the explicit
+        fold. f32_implicit: kernel 5's design on the implicit fold (6), 8 bytes
+        per half-row entry and pass. bf16 / f16: 2-byte codes with per-row scales
+        on the row-streaming kernel.
+        """
+        import torch
+        peak, _ = read_peak("hbm_gbs", 6800.0)
+        S, Mh, Nh = self.info["S"], self.system.Mh, self.system.Nh
+        nnz_half = self.info["nnz_half"]
+        lpc = self.tuned.get("lanes_per_col", 4) or 4
+        forms = [("f32", ss.F32, self.opts, 12, S),
+                 ("f32_rows", ss.F32, ss.solve_opts(self.iters, self.lam, kernel=3, lanes_per_col=lpc,
+                                                    block_threads=512), 12, S),
+                 ("f32_compact", ss.F32, ss.solve_opts(self.iters, self.lam, kernel=5, lanes_per_col=4,
+                                                       block_threads=512), 12, S),
+                 ("f32_implicit", ss.F32, ss.solve_opts(self.iters, self.lam, kernel=6, lanes_per_col=4,
+                                                        block_threads=512), 8, nnz_half),
+                 ("bf16", ss.BF16, ss.solve_opts(self.iters, self.lam, kernel=3, lanes_per_col=lpc,
+                                                 block_threads=512), 8, S),
+                 ("f16", ss.F16, ss.solve_opts(self.iters, self.lam, kernel=3, lanes_per_col=lpc,
+                                                block_threads=512), 8, S)]
+        out = {}
+        for name, dt, opts, bpe, entries in forms:
+            sysm = self.system if dt == ss.F32 else ss.fold_batch(geoms, dt)
+            p12 = torch.empty(sysm.Mh, 2, device=self.p12.device)
+            ss.fold_rhs(sysm, self.p_in, p12)
+            f12 = torch.zeros(sysm.Nh, 2, device=self.p12.device)
+            ts = []
+            for _ in range(3):
+                f12.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                ss.solve(sysm, p12, f12, opts)
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            ms = min(ts[1:])
+            alg = algorithmic_bytes_per_launch(entries, Mh, Nh, self.iters, batch_rows=Mh, bytes_per_entry=bpe)
+            out[name] = {"solve_ms": ms, "kernel": opts.kernel, "bytes_per_entry_per_pass": bpe,
+                         "algorithmic_bytes_per_launch": alg, "hbm_frac": alg / (ms / 1e3) / 1e9 / peak,
+                         "time_vs_f32_rows": None}
+            if dt != ss.F32:
+                del sysm
+                torch.cuda.empty_cache()
+        for name in out:
+            out[name]["time_vs_f32_rows"] = out[name]["solve_ms"] / out["f32_rows"]["solve_ms"]
+        out["note"] = ("same inputs and iterations; hbm_frac = each form's own algorithmic bytes / solve time / "
+                       "measured HBM peak")
+        return out
+
     def kernel_name(self):
         return {1: "sart_stream_kernel<TF32,LPC,batch> (CTA-wide staged tiles)",
                 2: "sart_resident_kernel<TF32,LPC>",
                 3: "sart_rows_kernel<TF32,LPC,batch> (row streaming, dynamically scheduled chunks)",
-                4: "sart_bulk_kernel<TF32,LPC,batch> (per-warp bulk-copy staging)"}.get(
+                4: "sart_bulk_kernel<TF32,LPC,batch> (per-warp bulk-copy staging)",
+                5: "sart_compact_kernel<TF32,explicit,batch> (row streaming in compacted index order)"}.get(
             self.tuned.get("kernel"), "sart_rows_kernel<TF32,LPC,batch> (library choice)")
 
     def config(self):
@@ -943,6 +1000,76 @@ def solvers_time_to_tol(ss, dev, rank, tol=1e-3):
     return out
 
 
+# Example 2 (Table 1) of the paper: a direct method on an unspecified CPU, seconds. Context only.
+TABLE1_PAPER_S = {32: {"full": 1.324, "split": 0.227}, 64: {"full": 73.434, "split": 3.233},
+                  128: {"full": 4948.770, "split": 76.473}}
+
+
+def table1_record(ss, dev, rank):
+    """The direct method at the three sizes of Example 2 (Table 1), split against full, on one GPU.
+
+    For each size: a seeded phantom, p = A f_true (consistent data, as a test
+    of the solver), then
+    - split: splitsart_direct_split (fold p, the normal-equation solves of A1
+      and A2, Theorem 1);
+    - full: splitsart_normal_solve on the full matrix (its CSR and CSC are built
+      on the host by mirroring the stored half rows, Eq. 2, outside the timed
+      region).
+    Each is timed 3 times with CUDA events (median). The error is
+    ||f - f_true|| / ||f_true||; the paper does not define its error.
+    """
+    import numpy as np
+    import scipy.sparse as sp
+    import torch
+    from paper_1902_10559_gb300.synthetic import random_phantom, table1_geometries
+    out = {}
+    for g in table1_geometries():
+        geom = ss.make_geometry(g)
+        sysm = ss.fold_system(geom, ss.F64)
+        f_img = torch.as_tensor(random_phantom(g, 7, 10, stream=1000 * rank), dtype=torch.float64, device=dev)
+        f_true = torch.empty(g.N, dtype=torch.float64, device=dev)
+        p = torch.empty(g.M, dtype=torch.float64, device=dev)
+        ss.project(sysm, f_img.reshape(-1), p, layout=ss.LAYOUT_IMAGE)
+        # The same image in snake order, for the error.
+        f12 = torch.empty(g.N // 2, 2, dtype=torch.float64, device=dev)
+        ss.fold_image(sysm, f_img.reshape(-1), f12, layout=ss.LAYOUT_IMAGE)
+        ss.recombine(sysm, f12, f_true)
+        rp, col, val = ss.full_csr(geom)
+        A = sp.csr_matrix((val, col, rp), shape=(g.M, g.N))
+        A.sort_indices()
+        T = sp.csc_matrix(A)
+        T.sort_indices()
+        to = lambda x, dt: torch.as_tensor(np.ascontiguousarray(x).astype(dt), device=dev)
+        csr = (to(A.indptr, np.int32), to(A.indices, np.int32), to(A.data, np.float64))
+        csc = (to(T.indptr, np.int32), to(T.indices, np.int32), to(T.data, np.float64))
+        res = {}
+        for mode in ("split", "full"):
+            solver = ss.DenseSolver(g.N // 2 if mode == "split" else g.N, device=dev)
+            f = torch.zeros(g.N, dtype=torch.float64, device=dev)
+            ts = []
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                if mode == "split":
+                    ss.direct_split(sysm, solver, p, f)
+                else:
+                    ss.normal_solve(solver, g.M, g.N, csr, csc, p, f)
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            err = float(((f - f_true).norm() / f_true.norm()).item())
+            res[mode] = {"ms": float(np.median(ts)), "status": solver.result(), "error_vs_f_true": err}
+            del solver
+            torch.cuda.empty_cache()
+        res["full_over_split"] = res["full"]["ms"] / res["split"]["ms"]
+        res["size"] = {"voxels": f"{g.nx}x{g.nz}", "positions": g.K, "bins": g.nb, "M": g.M, "N": g.N}
+        res["paper_cpu_s"] = TABLE1_PAPER_S[g.nx]
+        out[f"{g.nx}x{g.nz}"] = res
+    out["note"] = ("FP64 normal equations (B = A^T A, blocked Cholesky, two triangular solves) on the GPU; the paper's "
+                   "seconds are a direct method on an unspecified CPU, context only")
+    return out
+
+
 def time_to_tol_record(ss, dev, rank, stream):
     """Iterations and time to rho <= 1e-3 of each form against plain FP32 split-SART, on one GPU.
 
@@ -1050,6 +1177,7 @@ def run_native(args):
         torch.cuda.empty_cache()
         out["batch"] = batch_record(ss, dev, rank, stream, flush, local, args.batch_steps, 3)
         out["time_to_tol"] = time_to_tol_record(ss, dev, rank, stream)
+        out["table1_direct"] = table1_record(ss, dev, rank)
     if rank == 0 and not args.no_cpu_baseline:
         wl0 = WORKLOADS[args.workload]()
         _, out["cpu_baseline"] = oracle_throughput(wl0, args.cpu_seconds)
