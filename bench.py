@@ -52,7 +52,8 @@ UNIT = "voxel-updates/s"
 ITERS = 200
 LAMBDA = 0.8
 NOISE = 0.01
-KERNEL_SRC = os.path.join(ROOT, "paper_1902_10559_gb300", "csrc", "sart.cu")  # solve kernels
+KERNEL_SRC = os.path.join(ROOT, "paper_1902_10559_gb300", "csrc", "sart.cu")  # solve kernels 1-4
+STREAM_SRC = os.path.join(ROOT, "paper_1902_10559_gb300", "csrc", "stream.cu")  # solve kernels 5 and 6
 MULTI_SRC = os.path.join(ROOT, "paper_1902_10559_gb300", "csrc", "multi.cu")  # multi-RHS solve kernel
 PROFILES = os.path.join(ROOT, "profiles")
 # Kernel launches of one device fold of A: count, scan (3), fill, row compaction (5),
@@ -123,7 +124,8 @@ def read_peak(key: str, fallback: float):
         return fallback, "fallback"
 
 
-def profile_traffic(name: str, src: str = KERNEL_SRC, algorithmic_bytes: float | None = None):
+def profile_traffic(name: str, src: str = KERNEL_SRC, algorithmic_bytes: float | None = None,
+                    ratio_key: str = "dram_over_algorithmic"):
     """Per-launch DRAM bytes of the solve kernel from a committed ncu summary.
 
     A summary gives either ``dram_bytes_per_launch`` (captured on the bench's
@@ -144,7 +146,7 @@ def profile_traffic(name: str, src: str = KERNEL_SRC, algorithmic_bytes: float |
     m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     if m_bytes:
         return float(m_bytes.group(1))
-    m_ratio = re.search(r"dram_over_algorithmic:\s*([0-9.eE+]+)", txt)
+    m_ratio = re.search(re.escape(ratio_key) + r":\s*([0-9.eE+]+)", txt)
     if m_ratio and algorithmic_bytes:
         return float(m_ratio.group(1)) * algorithmic_bytes
     return None
@@ -382,12 +384,12 @@ class Batch(Realistic):
         # The timed graph also holds fold_rhs and recombine (about 0.1% of its bytes).
         peak, kind = read_peak("hbm_gbs", 6800.0)
         ach = alg / (solve_ms / 1e3) / 1e9
-        traffic = profile_traffic(self.profile, algorithmic_bytes=alg)
+        traffic = self.traffic(self.tuned.get("kernel"), alg)
         out = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                "traffic": traffic, "kernel": self.kernel_name(),
                "algorithmic_bytes_per_launch": alg, "peak_source": f"{kind} hbm_gbs",
-               "traffic_source": "ncu DRAM counters of the 64-slice case (one launch), scaled to this launch by "
-                                 "algorithmic bytes",
+               "traffic_source": "ncu DRAM counters of the same kernel on the 64-slice case (one launch), scaled to "
+                                 "this launch by algorithmic bytes",
                "note": "timed region = the replayed graph (fold of p, solve, recombine); inputs far exceed L2"}
         if traffic:
             out["dram_gbs"] = traffic / (solve_ms / 1e3) / 1e9
@@ -409,6 +411,16 @@ class Batch(Realistic):
             self.geometry_s["host_threads"] = min(32, os.cpu_count() or 1)
             del host, sysm
         return {"forms": self.form_times(ss, self.geoms), "geometry_s": self.geometry_s}
+
+    def traffic(self, kernel, alg):
+        """DRAM bytes of one launch of `kernel`, from the committed 64-slice capture of that kernel."""
+        if kernel == 5:
+            return profile_traffic("sart_compact_batch_fp32.txt", STREAM_SRC, alg)
+        if kernel == 6:
+            return profile_traffic("sart_compact_batch_fp32.txt", STREAM_SRC, alg, "dram_over_algorithmic_implicit")
+        if kernel == 3:
+            return profile_traffic(self.profile, KERNEL_SRC, alg)
+        return None
 
     def form_times(self, ss, geoms):
         """Solve time of the same inputs in each storage form and kernel, each with its own roofline.
@@ -455,6 +467,9 @@ class Batch(Realistic):
             out[name] = {"solve_ms": ms, "kernel": opts.kernel, "bytes_per_entry_per_pass": bpe,
                          "algorithmic_bytes_per_launch": alg, "hbm_frac": alg / (ms / 1e3) / 1e9 / peak,
                          "time_vs_f32_rows": None}
+            tr = self.traffic(opts.kernel, alg) if dt == ss.F32 else None
+            if tr:
+                out[name]["dram_frac"] = tr / (ms / 1e3) / 1e9 / peak
             if dt != ss.F32:
                 del sysm
                 torch.cuda.empty_cache()
