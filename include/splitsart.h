@@ -546,6 +546,19 @@ int splitsart_solve_multi(splitsart_system* sys, int nrhs, const void* p12_dev, 
                           void* stream);
 
 /*
+ * splitsart_solve_multi with the order in which the persistent launch takes
+ * its right-hand sides: order_dev[nrhs] (device int32) is a permutation of
+ * 0..nrhs-1, and queue position q solves right-hand side order_dev[q]
+ * (NULL: in index order, as splitsart_solve_multi). The layouts of p12_dev,
+ * f12_dev and info_dev stay indexed by right-hand side. With more right-hand
+ * sides than resident slots, the launch ends when the last long one does;
+ * handing out the longest first shortens that tail.
+ */
+int splitsart_solve_multi_ordered(splitsart_system* sys, int nrhs, const void* p12_dev, void* f12_dev,
+                                  const splitsart_solve_opts* opts, int rhs_per_cta, const int32_t* order_dev,
+                                  splitsart_solve_info* info_dev, void* stream);
+
+/*
  * Fallback rule of the warm start, per right-hand side r of a multi solve:
  * if info_warm[r].rho < info_base[r].rho, f12_dev[r] := f12_warm_dev[r];
  * otherwise f12_dev[r] (the base start) is kept. The rho values come from

@@ -49,6 +49,7 @@ struct MultiArgs {
     typename T::Vec2* f12;        // [nrhs][Nh]
     splitsart_solve_info* info;   // [nrhs]
     unsigned* queue;              // next right-hand side after the first wave (zeroed before the launch)
+    const int32_t* order;         // [nrhs] queue position -> right-hand side (null: in index order)
     int Mh, Nh, S, nrhs;
     int max_iters, check_every;
     double lambda, tol;
@@ -151,10 +152,11 @@ __global__ void __launch_bounds__(1024, 1) sart_multi_kernel(MultiArgs<T> a) {
         }
     };
 
-    // The first wave of right-hand sides is blockIdx.x * RC + r; later ones come from the queue.
+    // The first wave takes queue positions blockIdx.x * RC + r; later ones come from the queue.
+    // Position q holds right-hand side order[q] (q itself without an order).
     if (tid < RC) {
         const int r = blockIdx.x * RC + tid;
-        s_rhs[tid] = r < a.nrhs ? r : -1;
+        s_rhs[tid] = r < a.nrhs ? (a.order ? a.order[r] : r) : -1;
         s_k[tid] = 0;
     }
     __syncthreads();
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(1024, 1) sart_multi_kernel(MultiArgs<T> a) {
                 for (int r = 0; r < RC; ++r) {
                     if (fin >> r & 1u) {
                         const int nxt = (int)atomicAdd(a.queue, 1u) + (int)gridDim.x * RC;
-                        s_rhs[r] = nxt < a.nrhs ? nxt : -1;
+                        s_rhs[r] = nxt < a.nrhs ? (a.order ? a.order[nxt] : nxt) : -1;
                         s_k[r] = 0;
                     }
                     active += s_rhs[r] >= 0;
@@ -286,7 +288,7 @@ size_t multi_smem_bytes(const splitsart_system* s, int S, int RC) {
 
 template <class T, int RC>
 int launch_multi(splitsart_system* s, int S, int nrhs, const void* p12, void* f12, const splitsart_solve_opts& o,
-                 splitsart_solve_info* info, cudaStream_t st) {
+                 const int32_t* order, splitsart_solve_info* info, cudaStream_t st) {
     // Four lane groups per warp: up to 8 lanes per (row, right-hand side), about one
     // entry each for a slice whose rows hold tens of entries.
     constexpr int RPW = RC >= 4 ? 1 : 4 / RC;
@@ -340,6 +342,7 @@ int launch_multi(splitsart_system* s, int S, int nrhs, const void* p12, void* f1
     const int groups = (nrhs + RC - 1) / RC;
     const int grid = groups < nsm * per_sm ? groups : nsm * per_sm;
     a.queue = &s->ctl->work[0];
+    a.order = order;
     if ((e = cudaMemsetAsync(s->ctl, 0, sizeof(LaunchCtl), st)) != cudaSuccess)
         return cuda_fail(e, "solve_multi: memset");
     kern<<<grid, threads, dyn, st>>>(a);
@@ -349,13 +352,13 @@ int launch_multi(splitsart_system* s, int S, int nrhs, const void* p12, void* f1
 
 template <class T>
 int multi_typed(splitsart_system* s, int S, int nrhs, int rc, const void* p12, void* f12,
-                const splitsart_solve_opts& o, splitsart_solve_info* info, cudaStream_t st) {
+                const splitsart_solve_opts& o, const int32_t* order, splitsart_solve_info* info, cudaStream_t st) {
     switch (rc) {
-        case 1: return launch_multi<T, 1>(s, S, nrhs, p12, f12, o, info, st);
-        case 2: return launch_multi<T, 2>(s, S, nrhs, p12, f12, o, info, st);
-        case 4: return launch_multi<T, 4>(s, S, nrhs, p12, f12, o, info, st);
-        case 8: return launch_multi<T, 8>(s, S, nrhs, p12, f12, o, info, st);
-        case 16: return launch_multi<T, 16>(s, S, nrhs, p12, f12, o, info, st);
+        case 1: return launch_multi<T, 1>(s, S, nrhs, p12, f12, o, order, info, st);
+        case 2: return launch_multi<T, 2>(s, S, nrhs, p12, f12, o, order, info, st);
+        case 4: return launch_multi<T, 4>(s, S, nrhs, p12, f12, o, order, info, st);
+        case 8: return launch_multi<T, 8>(s, S, nrhs, p12, f12, o, order, info, st);
+        case 16: return launch_multi<T, 16>(s, S, nrhs, p12, f12, o, order, info, st);
     }
     return fail(SPLITSART_ERR_ARG, "solve_multi: rhs_per_cta must be 1, 2, 4, 8 or 16");
 }
@@ -398,9 +401,9 @@ extern "C" int splitsart_pick_start(const splitsart_system* s, int nrhs, const v
     return e == cudaSuccess ? SPLITSART_OK : cuda_fail(e, "pick_start: launch");
 }
 
-extern "C" int splitsart_solve_multi(splitsart_system* s, int nrhs, const void* p12_dev, void* f12_dev,
-                                     const splitsart_solve_opts* o, int rhs_per_cta, splitsart_solve_info* info_dev,
-                                     void* stream) {
+extern "C" int splitsart_solve_multi_ordered(splitsart_system* s, int nrhs, const void* p12_dev, void* f12_dev,
+                                             const splitsart_solve_opts* o, int rhs_per_cta, const int32_t* order_dev,
+                                             splitsart_solve_info* info_dev, void* stream) {
     splitsart::NvtxRange nvtx_range("splitsart_solve_multi");
     if (!s || !o || !p12_dev || !f12_dev || !info_dev) return fail(SPLITSART_ERR_ARG, "solve_multi: NULL argument");
     if (nrhs < 1) return fail(SPLITSART_ERR_ARG, "solve_multi: nrhs must be >= 1");
@@ -416,10 +419,16 @@ extern "C" int splitsart_solve_multi(splitsart_system* s, int nrhs, const void* 
     s->last = st;
     const int S = (int)fs.S;
     switch (s->dtype) {
-        case SPLITSART_F64: return multi_typed<TF64>(s, S, nrhs, per, p12_dev, f12_dev, *o, info_dev, st);
-        case SPLITSART_F32: return multi_typed<TF32>(s, S, nrhs, per, p12_dev, f12_dev, *o, info_dev, st);
-        case SPLITSART_BF16: return multi_typed<TBF16>(s, S, nrhs, per, p12_dev, f12_dev, *o, info_dev, st);
-        case SPLITSART_F16: return multi_typed<TF16>(s, S, nrhs, per, p12_dev, f12_dev, *o, info_dev, st);
+        case SPLITSART_F64: return multi_typed<TF64>(s, S, nrhs, per, p12_dev, f12_dev, *o, order_dev, info_dev, st);
+        case SPLITSART_F32: return multi_typed<TF32>(s, S, nrhs, per, p12_dev, f12_dev, *o, order_dev, info_dev, st);
+        case SPLITSART_BF16: return multi_typed<TBF16>(s, S, nrhs, per, p12_dev, f12_dev, *o, order_dev, info_dev, st);
+        case SPLITSART_F16: return multi_typed<TF16>(s, S, nrhs, per, p12_dev, f12_dev, *o, order_dev, info_dev, st);
     }
     return fail(SPLITSART_ERR_ARG, "solve_multi: unknown dtype");
+}
+
+extern "C" int splitsart_solve_multi(splitsart_system* s, int nrhs, const void* p12_dev, void* f12_dev,
+                                     const splitsart_solve_opts* o, int rhs_per_cta, splitsart_solve_info* info_dev,
+                                     void* stream) {
+    return splitsart_solve_multi_ordered(s, nrhs, p12_dev, f12_dev, o, rhs_per_cta, nullptr, info_dev, stream);
 }

@@ -81,6 +81,8 @@ _SIGS = {
     "splitsart_system_slices": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "splitsart_solve_result_slices": ([_P, ctypes.POINTER(SolveInfo), ctypes.c_int], ctypes.c_int),
     "splitsart_solve_multi": ([_P, ctypes.c_int, _P, _P, ctypes.POINTER(SolveOpts), ctypes.c_int, _P, _P], ctypes.c_int),
+    "splitsart_solve_multi_ordered": ([_P, ctypes.c_int, _P, _P, ctypes.POINTER(SolveOpts), ctypes.c_int, _P, _P, _P],
+                                      ctypes.c_int),
     "splitsart_pick_start": ([_P, ctypes.c_int, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "splitsart_refold": ([_P, _P], ctypes.c_int),
     "splitsart_system_info_get": ([_P, ctypes.POINTER(SystemInfo)], ctypes.c_int),
@@ -460,19 +462,24 @@ def solve_static(Mh: int, Nh: int, rp, col, val, cp, row, valT, invR, invC, p12,
         _stream_ptr(stream)))
 
 
-def solve_multi(system: System, p12, f12, opts: SolveOpts, info, rhs_per_cta: int = 0, stream=None) -> None:
+def solve_multi(system: System, p12, f12, opts: SolveOpts, info, rhs_per_cta: int = 0, stream=None,
+                order=None) -> None:
     """Solve nrhs right-hand sides at once. p12: [nrhs, Mh, 2], f12: [nrhs, Nh, 2] (in: f0, out: results).
 
     ``info`` is a CUDA uint8 tensor of nrhs * sizeof(SolveInfo) bytes; decode it with ``read_infos``.
+    ``order`` (optional CUDA int32 [nrhs], a permutation) is the order in which the launch takes them.
     """
     import torch
     vt = system.vec_dtype
     nrhs = p12.shape[0]
     if info.dtype != torch.uint8 or not info.is_cuda or info.numel() < nrhs * ctypes.sizeof(SolveInfo):
         raise ValueError("info: expected a CUDA uint8 tensor of nrhs * sizeof(SolveInfo) bytes")
-    _check(lib().splitsart_solve_multi(system.handle, nrhs, _dev_ptr(p12, 2 * system.Mh * nrhs, vt, "p12"),
-                                       _dev_ptr(f12, 2 * system.Nh * nrhs, vt, "f12"), ctypes.byref(opts),
-                                       rhs_per_cta, info.data_ptr(), _stream_ptr(stream)))
+    if order is not None and (order.dtype != torch.int32 or not order.is_cuda or order.numel() != nrhs):
+        raise ValueError("order: expected a CUDA int32 tensor of nrhs entries")
+    _check(lib().splitsart_solve_multi_ordered(system.handle, nrhs, _dev_ptr(p12, 2 * system.Mh * nrhs, vt, "p12"),
+                                               _dev_ptr(f12, 2 * system.Nh * nrhs, vt, "f12"), ctypes.byref(opts),
+                                               rhs_per_cta, None if order is None else order.data_ptr(),
+                                               info.data_ptr(), _stream_ptr(stream)))
 
 
 def pick_start(system: System, f12_warm, info_warm, info_base, f12, picked=None, stream=None) -> None:

@@ -100,12 +100,13 @@ class WarmStart:
             ss.fold_image(self._vec_for(b - a), img[a:b].reshape(-1), f12[a:b].reshape(-1, 2), layout=ss.LAYOUT_IMAGE)
         return f12
 
-    def solve(self, p12, f12, iters, tol=0.0):
-        """Solve all right-hand sides in place; returns the per-RHS info list and the raw device info."""
+    def solve(self, p12, f12, iters, tol=0.0, order=None):
+        """Solve all right-hand sides in place (in queue `order` if given); returns the raw device info."""
         import torch
         n = p12.shape[0]
         info = torch.zeros(n * ctypes.sizeof(ss.SolveInfo), dtype=torch.uint8, device=self.dev)
-        ss.solve_multi(self.system, p12, f12, ss.solve_opts(iters, self.lam, tol), info, rhs_per_cta=self.rhs_per_cta)
+        ss.solve_multi(self.system, p12, f12, ss.solve_opts(iters, self.lam, tol), info, rhs_per_cta=self.rhs_per_cta,
+                       order=order)
         return info
 
     # ---- 1. data ----
@@ -179,12 +180,15 @@ class WarmStart:
         f = torch.zeros(p12.shape[0], self.g.N // 2, 2, device=self.dev)
         return f, self.solve(p12, f, max_iters, tol)
 
-    def solve_warm(self, p12, tol, max_iters):
+    def solve_warm(self, p12, tol, max_iters, longest_first=True):
         """5 iterations, network, fold, fallback, continue. Returns (f12, info_early, info_rest, picked).
 
         A right-hand side that met tol within the first 5 iterations has
         stopped there; the continuation then returns it unchanged with 0
-        further iterations.
+        further iterations. With longest_first, the continuation's persistent
+        launch takes the right-hand sides in decreasing order of their start's
+        rho (the guess's where it was kept, else the 5-iteration image's), so
+        the slowest ones start first and the launch's tail is shorter.
         """
         import torch
         n = p12.shape[0]
@@ -195,7 +199,13 @@ class WarmStart:
         info_zero = self.solve(p12, torch.zeros_like(guess), 0)  # rho of a zero start (1, or 0 if p = 0)
         picked = torch.zeros(n, dtype=torch.int32, device=self.dev)
         ss.pick_start(self.system, guess, info_guess, info_zero, f_warm, picked)
-        info_rest = self.solve(p12, f_warm, max_iters - EARLY_ITERS, tol)
+        order = None
+        if longest_first:
+            rho_guess = np.array([i["rho"] for i in ss.read_infos(info_guess, n)])
+            rho_early = np.array([i["rho"] for i in ss.read_infos(info_early, n)])
+            rho_start = np.where(picked.cpu().numpy() != 0, rho_guess, rho_early)
+            order = torch.as_tensor(np.argsort(-rho_start, kind="stable").astype(np.int32), device=self.dev)
+        info_rest = self.solve(p12, f_warm, max_iters - EARLY_ITERS, tol, order=order)
         self._last_guess_info = info_guess
         return f_warm, info_early, info_rest, picked
 

@@ -161,3 +161,27 @@ def test_multi_rhs_already_converged_start_stops_at_zero(ss, case):
     infos = ss.read_infos(info, 2)
     assert infos[0]["iters"] == 0 and torch.equal(f12[0], start)
     assert infos[1]["iters"] > 0 and infos[1]["rho"] <= tol
+
+
+@pytest.mark.parametrize("rc", [1, 4])
+def test_queue_order_changes_nothing_but_the_schedule(ss, case, rc):
+    """splitsart_solve_multi_ordered: each right-hand side's arithmetic does not depend on its slot,
+    so any queue order returns bitwise the same f and the same iteration counts."""
+    g, A1, A2, ps = case
+    system = ss.fold_system(ss.make_geometry(g), ss.F32)
+    n = 40
+    vt = system.vec_dtype
+    p = torch.as_tensor(np.stack(ps[:n]), dtype=vt, device="cuda")
+    p12 = torch.empty(n, system.Mh, 2, dtype=vt, device="cuda")
+    for r in range(n):
+        ss.fold_rhs(system, p[r].contiguous(), p12[r])
+    outs = []
+    for order in (None, torch.arange(n - 1, -1, -1, dtype=torch.int32, device="cuda"),
+                  torch.as_tensor(np.random.default_rng(3).permutation(n).astype(np.int32), device="cuda")):
+        f12 = torch.zeros(n, system.Nh, 2, dtype=vt, device="cuda")
+        info = torch.zeros(n * ctypes.sizeof(ss.SolveInfo), dtype=torch.uint8, device="cuda")
+        ss.solve_multi(system, p12, f12, ss.solve_opts(300, 1.0, 2e-2), info, rhs_per_cta=rc, order=order)
+        outs.append((f12.cpu().numpy(), [i["iters"] for i in ss.read_infos(info, n)]))
+    assert len(set(outs[0][1])) > 1  # the right-hand sides stop at different iterations
+    for f, its in outs[1:]:
+        assert np.array_equal(f, outs[0][0]) and its == outs[0][1]
