@@ -2,9 +2,11 @@
 
 The network is trained on 5-iteration -> 500-iteration image pairs made by the
 library's own solver. On held-out phantoms:
-- it must lower the residual of the 5-iteration image;
-- a warm-started solve must reach the tolerance in fewer iterations than plain
-  split-SART from zero.
+- it must bring the 5-iteration image closer to the 500-iteration one;
+- at the metric's tolerance, rho <= 1e-3, a warm-started solve of 512 held-out
+  phantoms must take fewer iterations than plain split-SART from zero, and
+  less wall time (median of three launches each; the continuation takes its
+  right-hand sides longest first).
 The oracle's FP64 residual judges the warm-started result.
 """
 import numpy as np
@@ -39,14 +41,20 @@ def test_training_data_and_warm_start_gain(ws):
     guess = ws.predict(xe)
     # In image space the network brings the 5-iteration image closer to the 500-iteration image.
     assert (guess - te).norm() < 0.85 * (xe - te).norm()
-    tol = 1e-2
-    res = ws.compare(held, tol=tol, max_iters=20000)
+    tol = 1e-3
+    held = range(10**6, 10**6 + 512)
+    runs = [ws.compare(held, tol=tol, max_iters=40000) for _ in range(3)]
+    res = runs[0]
     assert np.all(res["rho_plain"] <= tol) and np.all(res["rho_warm"] <= tol)
-    # Gain: fewer iterations to the tolerance, for most phantoms and on average.
-    assert res["iters_warm"].mean() < 0.95 * res["iters_plain"].mean(), (res["iters_warm"].mean(), res["iters_plain"].mean())
-    assert np.mean(res["iters_warm"] < res["iters_plain"]) > 0.7
-    print(f"iterations to rho <= {tol}: plain {res['iters_plain'].mean():.0f}, warm {res['iters_warm'].mean():.0f}; "
-          f"time plain {res['ms_plain']:.1f} ms, warm {res['ms_warm']:.1f} ms; warm kept {res['warm_kept']:.2f}")
+    ms_plain = float(np.median([r["ms_plain"] for r in runs]))
+    ms_warm = float(np.median([r["ms_warm"] for r in runs]))
+    print(f"to rho <= {tol}: iterations plain {res['iters_plain'].mean():.0f}, warm {res['iters_warm'].mean():.0f}; "
+          f"time plain {ms_plain:.1f} ms, warm {ms_warm:.1f} ms; warm kept {res['warm_kept']:.2f}")
+    # Gain at the metric's tolerance: fewer iterations on average and for most phantoms, and less time.
+    assert res["iters_warm"].mean() < 0.97 * res["iters_plain"].mean(), (res["iters_warm"].mean(),
+                                                                        res["iters_plain"].mean())
+    assert np.mean(res["iters_warm"] < res["iters_plain"]) > 0.6
+    assert ms_warm < ms_plain, (ms_warm, ms_plain)
 
 
 def test_oracle_judges_warm_start_residual(ws):
