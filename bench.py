@@ -429,7 +429,8 @@ class Batch(Realistic):
         kernel (3). f32_compact: the compacted-order kernel (5) on the explicit
         fold. f32_implicit: kernel 5's design on the implicit fold (6), 8 bytes
         per half-row entry and pass. bf16 / f16: 2-byte codes with per-row scales
-        on the row-streaming kernel.
+        (8 bytes per entry and pass) on the row-streaming kernel; *_compact: the
+        same codes on kernel 5.
         """
         import torch
         peak, _ = read_peak("hbm_gbs", 6800.0)
@@ -446,10 +447,19 @@ class Batch(Realistic):
                  ("bf16", ss.BF16, ss.solve_opts(self.iters, self.lam, kernel=3, lanes_per_col=lpc,
                                                  block_threads=512), 8, S),
                  ("f16", ss.F16, ss.solve_opts(self.iters, self.lam, kernel=3, lanes_per_col=lpc,
-                                                block_threads=512), 8, S)]
+                                                block_threads=512), 8, S),
+                 ("bf16_compact", ss.BF16, ss.solve_opts(self.iters, self.lam, kernel=5, lanes_per_col=4,
+                                                         block_threads=512), 8, S),
+                 ("f16_compact", ss.F16, ss.solve_opts(self.iters, self.lam, kernel=5, lanes_per_col=4,
+                                                        block_threads=512), 8, S)]
         out = {}
+        reduced = {}
         for name, dt, opts, bpe, entries in forms:
-            sysm = self.system if dt == ss.F32 else ss.fold_batch(geoms, dt)
+            if dt != ss.F32 and dt not in reduced:
+                reduced.clear()
+                torch.cuda.empty_cache()
+                reduced[dt] = ss.fold_batch(geoms, dt)
+            sysm = self.system if dt == ss.F32 else reduced[dt]
             p12 = torch.empty(sysm.Mh, 2, device=self.p12.device)
             ss.fold_rhs(sysm, self.p_in, p12)
             f12 = torch.zeros(sysm.Nh, 2, device=self.p12.device)
@@ -470,9 +480,9 @@ class Batch(Realistic):
             tr = self.traffic(opts.kernel, alg) if dt == ss.F32 else None
             if tr:
                 out[name]["dram_frac"] = tr / (ms / 1e3) / 1e9 / peak
-            if dt != ss.F32:
-                del sysm
-                torch.cuda.empty_cache()
+            del sysm
+        reduced.clear()
+        torch.cuda.empty_cache()
         for name in out:
             out[name]["time_vs_f32_rows"] = out[name]["solve_ms"] / out["f32_rows"]["solve_ms"]
         out["note"] = ("same inputs and iterations; hbm_frac = each form's own algorithmic bytes / solve time / "

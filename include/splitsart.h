@@ -305,8 +305,8 @@ typedef struct splitsart_solve_opts {
                               its folded column carrying A1's sign: 8 instead of 12 bytes per entry and
                               pass in FP32; results differ from the explicit fold by rounding where a
                               ray and its mirror cross the same folded cell). 3 to 6 have no CTA
-                              barriers inside a pass. 5 and 6: FP64 and FP32 systems, lanes_per_col 4
-                              or 8; their first use builds the re-indexed copy of the matrix (4 bytes
+                              barriers inside a pass. 5: every value storage; 6: FP64 and FP32 systems;
+                              both lanes_per_col 4 or 8; their first use builds the re-indexed copy of the matrix (4 bytes
                               per entry and pass for 5, 8 or 12 for 6) and keeps it with the system */
     double timeout_ms;     /* limit of each grid-barrier wait; 0 = default (2000 ms) */
     int32_t inject_barrier_fault; /* test hook: the barrier also waits for a CTA that never comes */

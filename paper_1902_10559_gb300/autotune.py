@@ -88,8 +88,6 @@ def solve_candidates(system: ss.System) -> list[dict]:
                     out.append({"kernel": 2, "lanes_per_col": lpc, "block_threads": bt, "tile_entries": 0,
                                 "row_weight": rw})
     for kern, bts in ((4, (256, 384)), (3, (256, 512)), (5, (256, 512))):
-        if kern == 5 and system.dtype not in (ss.F64, ss.F32):
-            continue  # the compacted streaming kernel takes FP64 and FP32 systems
         for lpc in ((4, 8) if kern in (4, 5) else (4, 8, 16)):
             for bt in bts:
                 out.append({"kernel": kern, "lanes_per_col": lpc, "block_threads": bt, "tile_entries": 0})

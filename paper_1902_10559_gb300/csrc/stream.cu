@@ -10,7 +10,8 @@
 //   hot loop then indexes every vector directly, with no dependent index
 //   load between a row's sum and its update.
 // - Two storages. Kernel 5 streams the explicit fold (the pairs (a1, a2) of
-//   the folded CSR and CSC, 12 bytes per entry and pass in FP32). Kernel 6
+//   the folded CSR and CSC, 12 bytes per entry and pass in FP32; 8 with
+//   BF16/FP16 code pairs, whose row scale joins the row's data). Kernel 6
 //   streams the implicit fold: each entry of the half rows of A is stored
 //   once, as its compacted folded column with A1's sign in bit 31 and its
 //   length w, so that a1 = +-w and a2 = w (8 bytes per entry and pass). Eq. (2)
@@ -186,6 +187,7 @@ int build_stream_format(splitsart_system* s, int kind, const FoldStats& fs, cuda
     const size_t o_ri = take(sizeof(int32_t) * (size_t)nnz);
     const size_t o_rv = kind ? take(sizeof(V) * (size_t)nnz) : 0;
     const size_t o_ir = take(sizeof(N2) * (nr + 1));
+    const size_t o_sc = T::kQuant ? take(sizeof(float2) * (nr + 1)) : 0;
     const size_t o_ic = take(sizeof(N2) * (nc + 1));
     const size_t o_pc = take(sizeof(V2) * (nr + 1));
     const size_t o_uc = take(sizeof(V2) * (nr + 1));
@@ -202,6 +204,7 @@ int build_stream_format(splitsart_system* s, int kind, const FoldStats& fs, cuda
     F.ci = (int32_t*)(b + o_ci);
     F.ri = (int32_t*)(b + o_ri);
     F.ir = b + o_ir;
+    F.sc = T::kQuant ? (float2*)(b + o_sc) : nullptr;
     F.ic = b + o_ic;
     F.pc = b + o_pc;
     F.uc = b + o_uc;
@@ -270,8 +273,11 @@ int build_stream_format(splitsart_system* s, int kind, const FoldStats& fs, cuda
         if (rc) return fail_free(rc);
     }
     // Normalisers as applied, in compacted order.
-    st_gather_norm_kernel<N2><<<G, B, 0, st>>>(s->nzr, &s->stats->n_nzr, (const N2*)s->invR, (N2*)F.ir);
-    st_gather_norm_kernel<N2><<<G, B, 0, st>>>(s->nzc, &s->stats->n_nzc, (const N2*)s->invC, (N2*)F.ic);
+    st_gather_norm_kernel<N2><<<G, B, 0, st>>>(s->nzr, &s->stats->n_nzr,
+                                               (const N2*)(T::kQuant ? (const void*)s->wR : s->invR), (N2*)F.ir);
+    st_gather_norm_kernel<N2><<<G, B, 0, st>>>(s->nzc, &s->stats->n_nzc,
+                                               (const N2*)(T::kQuant ? (const void*)s->wC : s->invC), (N2*)F.ic);
+    if (T::kQuant) st_gather_norm_kernel<float2><<<G, B, 0, st>>>(s->nzr, &s->stats->n_nzr, s->scale, F.sc);
     st_slice_maps_kernel<<<G, B, 0, st>>>(s->nzr, s->nzc, s->stats, s->ns, s->sl_rows, s->sl_cols, F.qs, F.cs);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail_free(cuda_fail(e, "solve: streaming format"));
     F.built = 1;
@@ -323,6 +329,7 @@ struct StArgs {
     const Val* __restrict__ rv;
     const N2* __restrict__ ir;
     const N2* __restrict__ ic;
+    const float2* __restrict__ sc;  // BF16/FP16: compacted row scales
     V2* pc;
     V2* uc;
     V2* fc;
@@ -356,6 +363,14 @@ __device__ __forceinline__ float st_ld(const float* p) { return __ldcs(p); }
 __device__ __forceinline__ double st_ld(const double* p) { return __ldcs(p); }
 __device__ __forceinline__ float2 st_ld(const float2* p) { return __ldcs(p); }
 __device__ __forceinline__ double2 st_ld(const double2* p) { return __ldcs(p); }
+__device__ __forceinline__ __nv_bfloat162 st_ld(const __nv_bfloat162* p) {
+    const unsigned v = __ldcs(reinterpret_cast<const unsigned*>(p));
+    return *reinterpret_cast<const __nv_bfloat162*>(&v);
+}
+__device__ __forceinline__ __half2 st_ld(const __half2* p) {
+    const unsigned v = __ldcs(reinterpret_cast<const unsigned*>(p));
+    return *reinterpret_cast<const __half2*>(&v);
+}
 
 // The entries one lane holds for a step: U of each of R rows (or columns).
 template <class Val, int R, int U>
@@ -509,16 +524,18 @@ __global__ void __launch_bounds__(512, 1) sart_compact_kernel(StArgs<T, kImplici
     const int nrc = (n_nzr + kRowChunk - 1) / kRowChunk;
     const int ncc = (n_nzc + kColChunk - 1) / kColChunk;
     // Row data of a chunk: lane l <= 16 holds rp[q0 + l]; lane l < 16 holds p and 1/R of row q0 + l.
-    auto row_meta = [&](int ch, int& ptr, V2& pm, N2& irm) {
+    auto row_meta = [&](int ch, int& ptr, V2& pm, N2& irm, float2& scm) {
         const int q = ch * kRowChunk + lane;
         ptr = 0;
         pm = V2{};
         irm = N2{};
+        scm = float2{1.f, 1.f};
         if (ch < nrc) {
             if (lane <= kRowChunk) ptr = __ldg(a.rp + min(q, n_nzr));
             if (lane < kRowChunk && q < n_nzr) {
                 pm = ldcg(a.pc + q);
                 irm = ldg(a.ir + q);
+                if constexpr (T::kQuant) scm = ldg(a.sc + q);
             }
         }
     };
@@ -553,14 +570,16 @@ __global__ void __launch_bounds__(512, 1) sart_compact_kernel(StArgs<T, kImplici
         int ptr;
         V2 pm;
         N2 irm;
-        row_meta(chunk, ptr, pm, irm);
+        float2 scm;
+        row_meta(chunk, ptr, pm, irm, scm);
         while (chunk < nrc) {
             if (lane == 0) grab = atomicAdd(&a.ctl->work[0], 1u);
             const int nchunk = __shfl_sync(kFull, grab, 0);
             int nptr;
             V2 npm;
             N2 nirm;
-            row_meta(nchunk, nptr, npm, nirm);  // the next chunk's row data loads while this one runs
+            float2 nscm;
+            row_meta(nchunk, nptr, npm, nirm, nscm);  // the next chunk's row data loads while this one runs
             const int q0 = chunk * kRowChunk, nq = min(kRowChunk, n_nzr - q0);
             // Step (l, r): round r of chunk rows l .. l + R - 1 (warp-uniform bounds).
             auto row_bounds = [&](int l, int (&lo)[R], int (&hi)[R], int& len) {
@@ -611,6 +630,10 @@ __global__ void __launch_bounds__(512, 1) sart_compact_kernel(StArgs<T, kImplici
                                 t1 = s1[h];
                                 t2 = s2[h];
                             }
+                        if constexpr (T::kQuant) {  // codes times the row's scale; 1/R already holds it for u
+                            t1 *= scm.x;
+                            t2 *= scm.y;
+                        }
                         const Acc r1 = pm.x - t1, r2 = pm.y - t2;
                         stcg(a.uc + q0 + lane, V2{r1 * irm.x, r2 * irm.y});
                         if constexpr (kBatch) __stcg(a.rr + q0 + lane, (double)(r1 * r1 + r2 * r2));
@@ -634,6 +657,7 @@ __global__ void __launch_bounds__(512, 1) sart_compact_kernel(StArgs<T, kImplici
             ptr = nptr;
             pm = npm;
             irm = nirm;
+            scm = nscm;
         }
         if constexpr (!kBatch) {
             const double t = warp_sum(rr.sum());
@@ -824,11 +848,13 @@ namespace {
 // implicit (5 and 4), against 817/682 ms for one row per step with the next
 // step's loads issued ahead, 788/740 ms for two rows with them, 672/615 ms for
 // one row with 8 entries per lane, and 1054/662 ms for two rows with 6 and 5.
-template <bool kImplicit, bool kWide>
+// kNarrow: 4-byte values per entry (the implicit fold's FP32 lengths, or BF16/FP16
+// code pairs); kWide: FP64 vectors.
+template <bool kNarrow, bool kWide>
 struct PipeShape {
     static constexpr int R = 2;
-    static constexpr int UF = kWide ? 2 : (kImplicit ? 5 : 4);
-    static constexpr int UB = kWide ? 2 : (kImplicit ? 4 : 3);
+    static constexpr int UF = kWide ? 2 : (kNarrow ? 5 : 4);
+    static constexpr int UB = kWide ? 2 : (kNarrow ? 4 : 3);
 };
 
 template <class T, bool kImplicit, int LPC>
@@ -837,7 +863,7 @@ int launch_pipe(splitsart_system* s, const void* p12, void* f12, const splitsart
     using N2 = typename T::KNorm2;
     using Val = typename Stor<T, kImplicit>::Val;
     constexpr bool kWide = sizeof(V2) == 16;
-    using Shape = PipeShape<kImplicit, kWide>;
+    using Shape = PipeShape<kImplicit || T::kQuant, kWide>;  // 2-byte codes take registers like the implicit fold
     constexpr int UF = Shape::UF, UB = Shape::UB, R = Shape::R;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -876,6 +902,7 @@ int launch_pipe(splitsart_system* s, const void* p12, void* f12, const splitsart
     a.rv = (const Val*)F.rv;
     a.ir = (const N2*)F.ir;
     a.ic = (const N2*)F.ic;
+    a.sc = F.sc;
     a.pc = (V2*)F.pc;
     a.uc = (V2*)F.uc;
     a.fc = (V2*)F.fc;
@@ -930,13 +957,15 @@ int launch_pipe_lpc(splitsart_system* s, const void* p12, void* f12, const split
 
 int run_solve_stream(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o, cudaStream_t st) {
     const bool imp = o.kernel == 6;
+    if (!imp && s->dtype == SPLITSART_BF16) return launch_pipe_lpc<TBF16, false>(s, p12, f12, o, st);
+    if (!imp && s->dtype == SPLITSART_F16) return launch_pipe_lpc<TF16, false>(s, p12, f12, o, st);
     switch (s->dtype) {
         case SPLITSART_F64:
             return imp ? launch_pipe_lpc<TF64, true>(s, p12, f12, o, st) : launch_pipe_lpc<TF64, false>(s, p12, f12, o, st);
         case SPLITSART_F32:
             return imp ? launch_pipe_lpc<TF32, true>(s, p12, f12, o, st) : launch_pipe_lpc<TF32, false>(s, p12, f12, o, st);
     }
-    return fail(SPLITSART_ERR_ARG, "solve: kernels 5 and 6 take FP64 and FP32 systems");
+    return fail(SPLITSART_ERR_ARG, "solve: kernel 6 takes FP64 and FP32 systems (kernel 5 also BF16 and FP16)");
 }
 
 }  // namespace splitsart

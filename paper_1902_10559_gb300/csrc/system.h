@@ -69,6 +69,7 @@ struct StreamFmt {
     int32_t* ri = nullptr;   // CSC indices: compacted rows (implicit: A1's sign in bit 31)
     const void* rv = nullptr;  // CSC values
     void* ir = nullptr;      // [n_nzr] 1/R as applied, compacted
+    float2* sc = nullptr;    // [n_nzr] row scales of BF16/FP16 codes, compacted
     void* ic = nullptr;      // [n_nzc] 1/C as applied, compacted
     void* pc = nullptr;      // [n_nzr] pairs: p of the launch, compacted
     void* uc = nullptr;      // [n_nzr] pairs: u

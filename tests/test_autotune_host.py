@@ -59,7 +59,7 @@ def test_candidates_are_valid_launch_shapes(dtype, nslices):
         if c["kernel"] in (2, 3, 5):
             assert bt <= 512
         if c["kernel"] == 5:
-            assert dtype in (ss.F64, ss.F32) and c["lanes_per_col"] in (4, 8)
+            assert c["lanes_per_col"] in (4, 8)
         if c["kernel"] == 4:
             assert bt <= 384 and c["lanes_per_col"] in (4, 8)
         if c["kernel"] == 1:

@@ -210,3 +210,21 @@ def test_rejected_shapes(ss, tiny):
     with pytest.raises(ss.SplitSartError) as e:
         ss.solve(s32, p12, f12, ss.solve_opts(5, 1.0, kernel=5, lanes_per_col=2))
     assert e.value.code == ss.ERR_ARG
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_reduced_precision_codes_on_kernel_5(ss, tiny, fmt):
+    """BF16/FP16 codes with per-row scales on the compacted kernel, against the oracle on the stored values."""
+    A, p, A1, A2, p1, p2 = tiny
+    sysm = ss.fold_system(ss.make_geometry(TINY), ss.DTYPE_NAMES[fmt])
+    out = sysm.export()
+    shape = (TINY.M // 2, TINY.N // 2)
+    H1 = sp.csr_matrix((out["a1"], out["col"], out["row_ptr"]), shape=shape)
+    H2 = sp.csr_matrix((out["a2"], out["col"], out["row_ptr"]), shape=shape)
+    ref = osart.split_sart(H1, H2, p1, p2, 1.0, 200)
+    infos, f12, f = solve(ss, sysm, p, 200, 1.0, kernel=5)
+    close(f, osplit.recombine(ref["f1"], ref["f2"]), 1e-4, f"{fmt} codes, kernel 5")
+    close_scalar(infos[0]["rho"], ref["rho"], 1e-4, "rho")
+    # The row-streaming kernel on the same codes: the same arithmetic, the same f up to FP32 rounding.
+    _, f12_3, _ = solve(ss, sysm, p, 200, 1.0, kernel=3)
+    close(f12, f12_3, 1e-5, f"{fmt}: kernel 5 vs kernel 3")
