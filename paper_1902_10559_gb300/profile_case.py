@@ -2,7 +2,7 @@
 
 Usage:
     python -m paper_1902_10559_gb300.profile_case realistic [--iters N] [--kernel K] [--lpc L] [--threads T]
-    python -m paper_1902_10559_gb300.profile_case batch --slices S [--iters N] [--kernel K] ...
+    python -m paper_1902_10559_gb300.profile_case batch --slices S [--iters N] [--kernel K] [--dtype f32|bf16|f16] ...
     python -m paper_1902_10559_gb300.profile_case multi [--nrhs R] [--iters N] [--rc C] [--dtype f32|bf16|f16]
     python -m paper_1902_10559_gb300.profile_case cnn [--batch B]
 
@@ -32,7 +32,8 @@ def main():
     ap.add_argument("--nrhs", type=int, default=64)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--rc", type=int, default=0, help="multi: right-hand sides per CTA (0 = library choice)")
-    ap.add_argument("--dtype", choices=["f32", "bf16", "f16"], default="f32", help="multi: matrix value storage")
+    ap.add_argument("--dtype", choices=["f32", "bf16", "f16"], default="f32",
+                    help="multi and batch: matrix value storage")
     args = ap.parse_args()
     dev = torch.device("cuda")
 
@@ -47,7 +48,7 @@ def main():
             sysm = ss.fold_system(ss.make_geometry(REALISTIC), ss.F32)
         else:
             gs = batch_geometries()[: args.slices]
-            sysm = ss.fold_batch([ss.make_geometry(g) for g in gs], ss.F32)
+            sysm = ss.fold_batch([ss.make_geometry(g) for g in gs], ss.DTYPE_NAMES[args.dtype])
         p = torch.empty(sysm.M, device=dev)
         ss.project(sysm, phantoms(gs, 2 if args.case == "realistic" else 3, 12), p, layout=ss.LAYOUT_IMAGE)
         p12 = torch.empty(sysm.Mh, 2, device=dev)
