@@ -259,7 +259,42 @@ class Realistic:
         if traffic:
             out["dram_gbs"] = traffic / (solve_ms / 1e3) / 1e9
             out["dram_frac"] = out["dram_gbs"] / peak
+        out["on_chip"] = self.latency_floor(ss, solve_ms)
         return out
+
+    def latency_floor(self, ss, solve_ms):
+        """The resident kernel's latency bound, measured.
+
+        The same kernel and launch shape on the tiny slice (S = 3,394 entries over
+        152 CTAs: a few rows and columns each) runs every per-iteration step that
+        does not scale with the matrix: the two grid barriers, the norm reduction,
+        the stop test, and one round of dependent gathers each way. Its time per
+        iteration is the floor under this kernel; frac = floor / the realistic
+        slice's time per iteration.
+        """
+        import torch
+        from paper_1902_10559_gb300.synthetic import TINY
+        if self.tuned.get("kernel") != 2:
+            return None
+        tiny = ss.fold_system(ss.make_geometry(TINY), ss.F32)
+        p12 = torch.zeros(TINY.M // 2, 2, device=self.p12.device)
+        p12[:, 1] = 1.0
+        f12 = torch.zeros(TINY.N // 2, 2, device=self.p12.device)
+        ts = []
+        for _ in range(4):
+            f12.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ss.solve(tiny, p12, f12, self.opts)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        floor_us = min(ts[1:]) * 1e3 / self.iters
+        per_us = solve_ms * 1e3 / self.iters
+        return {"bound": "latency", "floor_us_per_iteration": floor_us, "us_per_iteration": per_us,
+                "frac": floor_us / per_us,
+                "floor_from": "the same kernel and launch shape on the tiny slice (3,394 entries): two grid barriers, "
+                              "the norm reduction, the stop test and one round of dependent gathers each way"}
 
     def extra(self, ss):
         """Workload-specific keys added to the JSON line."""
