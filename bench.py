@@ -54,6 +54,7 @@ LAMBDA = 0.8
 NOISE = 0.01
 KERNEL_SRC = os.path.join(ROOT, "paper_1902_10559_gb300", "csrc", "sart.cu")  # solve kernels 1-4
 STREAM_SRC = os.path.join(ROOT, "paper_1902_10559_gb300", "csrc", "stream.cu")  # solve kernels 5 and 6
+RING_SRC = os.path.join(ROOT, "paper_1902_10559_gb300", "csrc", "ring.cu")  # solve kernels 7 and 8
 MULTI_SRC = os.path.join(ROOT, "paper_1902_10559_gb300", "csrc", "multi.cu")  # multi-RHS solve kernel
 PROFILES = os.path.join(ROOT, "profiles")
 # Kernel launches of one device fold of A: count, scan (3), fill, row compaction (5),
@@ -453,6 +454,10 @@ class Batch(Realistic):
             return profile_traffic("sart_compact_batch_fp32.txt", STREAM_SRC, alg)
         if kernel == 6:
             return profile_traffic("sart_compact_batch_fp32.txt", STREAM_SRC, alg, "dram_over_algorithmic_implicit")
+        if kernel == 7:
+            return profile_traffic("sart_ring_batch_fp32.txt", RING_SRC, alg)
+        if kernel == 8:
+            return profile_traffic("sart_ring_batch_fp32.txt", RING_SRC, alg, "dram_over_algorithmic_implicit")
         if kernel == 3:
             return profile_traffic(self.profile, KERNEL_SRC, alg)
         return None
@@ -463,9 +468,11 @@ class Batch(Realistic):
         f32: the timed solve (autotuned launch shape). f32_rows: the row-streaming
         kernel (3). f32_compact: the compacted-order kernel (5) on the explicit
         fold. f32_implicit: kernel 5's design on the implicit fold (6), 8 bytes
-        per half-row entry and pass. bf16 / f16: 2-byte codes with per-row scales
-        (8 bytes per entry and pass) on the row-streaming kernel; *_compact: the
-        same codes on kernel 5.
+        per half-row entry and pass. f32_ring / f32_ring_implicit: the same two
+        folds fed through a producer warp's shared-memory ring (kernels 7 and 8).
+        bf16 / f16: 2-byte codes with per-row scales (8 bytes per entry and pass)
+        on the row-streaming kernel; *_compact: the same codes on kernel 5;
+        bf16_ring: on kernel 7.
         """
         import torch
         peak, _ = read_peak("hbm_gbs", 6800.0)
@@ -479,12 +486,16 @@ class Batch(Realistic):
                                                        block_threads=512), 12, S),
                  ("f32_implicit", ss.F32, ss.solve_opts(self.iters, self.lam, kernel=6, lanes_per_col=4,
                                                         block_threads=512), 8, nnz_half),
+                 ("f32_ring", ss.F32, ss.solve_opts(self.iters, self.lam, kernel=7, lanes_per_col=4), 12, S),
+                 ("f32_ring_implicit", ss.F32, ss.solve_opts(self.iters, self.lam, kernel=8, lanes_per_col=4), 8,
+                  nnz_half),
                  ("bf16", ss.BF16, ss.solve_opts(self.iters, self.lam, kernel=3, lanes_per_col=lpc,
                                                  block_threads=512), 8, S),
-                 ("f16", ss.F16, ss.solve_opts(self.iters, self.lam, kernel=3, lanes_per_col=lpc,
-                                                block_threads=512), 8, S),
                  ("bf16_compact", ss.BF16, ss.solve_opts(self.iters, self.lam, kernel=5, lanes_per_col=4,
                                                          block_threads=512), 8, S),
+                 ("bf16_ring", ss.BF16, ss.solve_opts(self.iters, self.lam, kernel=7, lanes_per_col=4), 8, S),
+                 ("f16", ss.F16, ss.solve_opts(self.iters, self.lam, kernel=3, lanes_per_col=lpc,
+                                                block_threads=512), 8, S),
                  ("f16_compact", ss.F16, ss.solve_opts(self.iters, self.lam, kernel=5, lanes_per_col=4,
                                                         block_threads=512), 8, S)]
         out = {}
@@ -529,7 +540,10 @@ class Batch(Realistic):
                 2: "sart_resident_kernel<TF32,LPC>",
                 3: "sart_rows_kernel<TF32,LPC,batch> (row streaming, dynamically scheduled chunks)",
                 4: "sart_bulk_kernel<TF32,LPC,batch> (per-warp bulk-copy staging)",
-                5: "sart_compact_kernel<TF32,explicit,batch> (row streaming in compacted index order)"}.get(
+                5: "sart_compact_kernel<TF32,explicit,batch> (row streaming in compacted index order)",
+                6: "sart_compact_kernel<TF32,implicit,batch> (row streaming in compacted index order)",
+                7: "sart_ring_kernel<TF32,explicit,batch> (compacted order through a producer warp's ring)",
+                8: "sart_ring_kernel<TF32,implicit,batch> (compacted order through a producer warp's ring)"}.get(
             self.tuned.get("kernel"), "sart_rows_kernel<TF32,LPC,batch> (library choice)")
 
     def config(self):

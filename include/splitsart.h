@@ -295,7 +295,7 @@ typedef struct splitsart_solve_opts {
                               larger values run 512). Kernel 4: at most 384 (default 384) */
     int32_t ctas_per_sm;   /* 0 = as many as fit */
     int32_t lanes_per_col; /* back-projection lanes per column, 0 = default (8); 1,2,4,8,16,32 */
-    int32_t kernel;        /* 0 = choose (2 if the system fits on chip, else 3); 1 = stream the matrix in
+    int32_t kernel;        /* 0 = choose (2 if the system fits on chip, else 3); 0-8. 1 = stream the matrix in
                               CTA-wide tiles; 2 = keep it in shared memory; 3 = stream it row by row
                               through registers; 4 = stream it per warp through shared memory with
                               bulk asynchronous copies (lanes_per_col 4 or 8 only); 5 = stream it row by
@@ -307,10 +307,20 @@ typedef struct splitsart_solve_opts {
                               ray and its mirror cross the same folded cell). 3 to 6 have no CTA
                               barriers inside a pass. 5: every value storage; 6: FP64 and FP32 systems;
                               both lanes_per_col 4 or 8; their first use builds the re-indexed copy of the matrix (4 bytes
-                              per entry and pass for 5, 8 or 12 for 6) and keeps it with the system */
-    double timeout_ms;     /* limit of each grid-barrier wait; 0 = default (2000 ms) */
+                              per entry and pass for 5, 8 or 12 for 6) and keeps it with the system;
+                              7 and 8 = kernels 5 and 6 with the matrix fed through a shared-memory ring:
+                              per CTA one producer warp copies chunks of rows (columns) with bulk asynchronous
+                              copies and the other warps only gather and sum; they return kernel 5's and 6's
+                              f bit for bit at equal lanes_per_col. tile_entries is their chunk entry target
+                              (0 = about 48 KB of entries per chunk); a chunk must fit in the ring (about
+                              225 KB of shared memory), else SPLITSART_ERR_ARG. block_threads and
+                              ctas_per_sm are not used (one CTA per SM). Their first use also makes the chunk
+                              plans (one synchronisation) and keeps them with the system */
+    double timeout_ms;     /* limit of each grid-barrier wait (kernels 4, 7, 8: also of each wait on a bulk copy
+                              or a ring release); 0 = default (2000 ms) */
     int32_t inject_barrier_fault; /* test hook: the barrier also waits for a CTA that never comes */
-    int32_t tile_entries;  /* streaming kernel: entries staged per tile, 0 = default; multiple of 1024 in [1024, 16384] */
+    int32_t tile_entries;  /* kernel 1: entries staged per tile; kernels 7 and 8: chunk entry target. 0 = default;
+                              else a multiple of 1024 in [1024, 16384] */
     int32_t row_weight;    /* kernel 2: when rows are dealt to CTAs, each row weighs this many entries more than
                               its length (a row's fixed cost). 0 = default: the heaviest of 240, 160, 80, 40, 0
                               whose plan fits in shared memory; a value that does not fit falls back the same way */

@@ -5,9 +5,10 @@ cached per (device, storage type, problem class) in a JSON file:
 $SPLITSART_TUNE_CACHE, or ~/.cache/splitsart/tune.json.
 
 - Persistent solve: kernel (shared-memory resident, tile streaming, row
-  streaming through registers, row streaming in compacted index order, or
-  per-warp bulk-staged streaming), tile entries per CTA, lanes per column in
-  the back-projection, threads per CTA.
+  streaming through registers, row streaming in compacted index order fed
+  per warp or through a producer warp's shared-memory ring, or per-warp
+  bulk-staged streaming), tile entries per CTA (chunk entries of the ring),
+  lanes per column in the back-projection, threads per CTA.
 - Multi-right-hand-side solve: right-hand sides per CTA, threads per CTA.
 
 The tuner only chooses among launch shapes of the same arithmetic, so every
@@ -91,6 +92,9 @@ def solve_candidates(system: ss.System) -> list[dict]:
         for lpc in ((4, 8) if kern in (4, 5) else (4, 8, 16)):
             for bt in bts:
                 out.append({"kernel": kern, "lanes_per_col": lpc, "block_threads": bt, "tile_entries": 0})
+    for lpc in (4, 8):  # kernel 7 ignores block_threads; tile_entries is its chunk entry target
+        for te in (0, 2048, 6144):
+            out.append({"kernel": 7, "lanes_per_col": lpc, "block_threads": 0, "tile_entries": te})
     for lpc in (4, 8, 16):
         for te in (4096, 8192, 12288):
             if system.dtype == ss.F64 and te > 8192:

@@ -24,7 +24,7 @@ LIB = os.path.join(HERE, "libsplitsart.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["api.cu", "fold.cu", "sart.cu", "os_sart.cu", "cgls.cu", "stream.cu", "direct.cu", "multi.cu", "cnn.cu", "cnn_mma.cu", "geometry_gpu.cu"]
+CU_SOURCES = ["api.cu", "fold.cu", "sart.cu", "os_sart.cu", "cgls.cu", "stream.cu", "ring.cu", "direct.cu", "multi.cu", "cnn.cu", "cnn_mma.cu", "geometry_gpu.cu"]
 # The device tracer must round like the host tracer: no fused multiply-adds.
 CU_FLAGS = {"geometry_gpu.cu": ["-fmad=false"]}
 CPP_SOURCES = ["geometry.cpp"]

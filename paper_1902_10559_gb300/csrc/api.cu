@@ -347,8 +347,10 @@ extern "C" void splitsart_system_destroy(splitsart_system* s) {
     if (!s) return;
     if (s->base || s->res_alloc || s->os_alloc || s->cg_alloc || s->st[0].alloc || s->st[1].alloc)
         cudaStreamSynchronize(s->last);
-    for (auto& f : s->st)
+    for (auto& f : s->st) {
         if (f.alloc) cudaFree(f.alloc);
+        if (f.ring_alloc) cudaFree(f.ring_alloc);
+    }
     if (s->base) cudaFree(s->base);
     if (s->res_alloc) cudaFree(s->res_alloc);
     if (s->os_alloc) cudaFree(s->os_alloc);
@@ -480,7 +482,7 @@ extern "C" int splitsart_solve(splitsart_system* s, const void* p12, void* f12, 
     if ((s->Mh > 0 && !p12) || (s->Nh > 0 && !f12)) return fail(SPLITSART_ERR_ARG, "solve: NULL vector");
     if (o->max_iters < 0 || o->max_iters > 500000)
         return fail(SPLITSART_ERR_ARG, "solve: max_iters must be in [0, 500000]");
-    if (o->kernel < 0 || o->kernel > 6) return fail(SPLITSART_ERR_ARG, "solve: kernel must be in [0, 6]");
+    if (o->kernel < 0 || o->kernel > 8) return fail(SPLITSART_ERR_ARG, "solve: kernel must be in [0, 8]");
     if (o->tile_entries != 0 && (o->tile_entries % 1024 != 0 || o->tile_entries < 1024 || o->tile_entries > 16384))
         return fail(SPLITSART_ERR_ARG, "solve: tile_entries must be 0 or a multiple of 1024 in [1024, 16384]");
     if (!(o->lambda > 0.0) || !std::isfinite(o->lambda)) return fail(SPLITSART_ERR_ARG, "solve: lambda must be > 0");
@@ -489,6 +491,7 @@ extern "C" int splitsart_solve(splitsart_system* s, const void* p12, void* f12, 
     if (!(o->timeout_ms >= 0.0)) return fail(SPLITSART_ERR_ARG, "solve: timeout_ms must be >= 0");
     s->last = (cudaStream_t)stream;
     if (o->kernel == 5 || o->kernel == 6) return run_solve_stream(s, p12, f12, *o, (cudaStream_t)stream);
+    if (o->kernel == 7 || o->kernel == 8) return run_solve_ring(s, p12, f12, *o, (cudaStream_t)stream);
     return run_solve(s, p12, f12, *o, (cudaStream_t)stream);
 }
 

@@ -33,15 +33,12 @@
 #include <algorithm>
 #include <vector>
 
-#include "device_common.cuh"
-#include "system.h"
+#include "stream_common.cuh"
 
 namespace splitsart {
 
 namespace {
 
-constexpr uint32_t kSignBit = 0x80000000u;
-constexpr uint32_t kIndexMask = 0x7fffffffu;
 constexpr int kSortCap = 512;  // column entries staged in shared memory by the sort (longer: global)
 
 size_t st_align(size_t x) { return (x + 255) & ~size_t(255); }
@@ -284,107 +281,6 @@ int build_stream_format(splitsart_system* s, int kind, const FoldStats& fs, cuda
     return SPLITSART_OK;
 }
 
-}  // namespace
-}  // namespace splitsart
-
-namespace splitsart {
-namespace {
-
-// Storage traits of the streamed matrix: how one entry gives its compacted
-// index and the pair (a1, a2).
-template <class T, bool kImplicit>
-struct Stor;
-template <class T>
-struct Stor<T, false> {  // explicit fold: index, (a1, a2)
-    using Val = typename T::Pair;
-    __device__ static __forceinline__ int col(int32_t idx) { return idx; }
-    __device__ static __forceinline__ void get(int32_t idx, Val v, int& j, typename T::Acc& a1,
-                                               typename T::Acc& a2) {
-        j = idx;
-        T::decode(v, a1, a2);
-    }
-};
-template <class T>
-struct Stor<T, true> {  // implicit fold: index with A1's sign in bit 31, w
-    using Val = decltype(typename T::Vec2{}.x);
-    __device__ static __forceinline__ int col(int32_t idx) { return (int)((uint32_t)idx & kIndexMask); }
-    __device__ static __forceinline__ void get(int32_t idx, Val v, int& j, typename T::Acc& a1,
-                                               typename T::Acc& a2) {
-        j = (int)((uint32_t)idx & kIndexMask);
-        a2 = v;
-        a1 = idx < 0 ? -v : v;
-    }
-};
-
-template <class T, bool kImplicit>
-struct StArgs {
-    using Val = typename Stor<T, kImplicit>::Val;
-    using V2 = typename T::Vec2;
-    using N2 = typename T::KNorm2;
-    const int32_t* __restrict__ rp;
-    const int32_t* __restrict__ ci;
-    const Val* __restrict__ cv;
-    const int32_t* __restrict__ cp;
-    const int32_t* __restrict__ ri;
-    const Val* __restrict__ rv;
-    const N2* __restrict__ ir;
-    const N2* __restrict__ ic;
-    const float2* __restrict__ sc;  // BF16/FP16: compacted row scales
-    V2* pc;
-    V2* uc;
-    V2* fc;
-    double* rr;
-    const int32_t* __restrict__ qs;
-    const int32_t* __restrict__ cs;
-    double* pz;
-    const V2* __restrict__ p12;
-    V2* f12;
-    const int32_t* __restrict__ nzr;
-    const int32_t* __restrict__ nzc;
-    const int32_t* __restrict__ zr;
-    const FoldStats* stats;
-    double* partials;
-    LaunchCtl* ctl;
-    SolveResultDev* result;
-    int Mh;
-    int ns;
-    const long long* sl_rows;
-    SliceSolve* sl_solve;
-    int* ndone;
-    int max_iters, check_every;
-    double lambda, tol, tol2_hi;
-    unsigned long long timeout_ns;
-    unsigned expected;
-};
-
-// Index and value loads with the streaming hint (each is read once per pass).
-__device__ __forceinline__ int32_t st_ld(const int32_t* p) { return __ldcs(p); }
-__device__ __forceinline__ float st_ld(const float* p) { return __ldcs(p); }
-__device__ __forceinline__ double st_ld(const double* p) { return __ldcs(p); }
-__device__ __forceinline__ float2 st_ld(const float2* p) { return __ldcs(p); }
-__device__ __forceinline__ double2 st_ld(const double2* p) { return __ldcs(p); }
-__device__ __forceinline__ __nv_bfloat162 st_ld(const __nv_bfloat162* p) {
-    const unsigned v = __ldcs(reinterpret_cast<const unsigned*>(p));
-    return *reinterpret_cast<const __nv_bfloat162*>(&v);
-}
-__device__ __forceinline__ __half2 st_ld(const __half2* p) {
-    const unsigned v = __ldcs(reinterpret_cast<const unsigned*>(p));
-    return *reinterpret_cast<const __half2*>(&v);
-}
-
-// The entries one lane holds for a step: U of each of R rows (or columns).
-template <class Val, int R, int U>
-struct StepBuf {
-    int32_t ia[R][U];
-    Val va[R][U];
-};
-
-}  // namespace
-}  // namespace splitsart
-
-namespace splitsart {
-namespace {
-
 // R: rows (columns per lane group) per step.
 template <class T, bool kImplicit, bool kBatch, int LPC, int UF, int UB, int R>
 __global__ void __launch_bounds__(512, 1) sart_compact_kernel(StArgs<T, kImplicit> a) {
@@ -402,81 +298,18 @@ __global__ void __launch_bounds__(512, 1) sart_compact_kernel(StArgs<T, kImplici
     __shared__ double s_tpp;
     __shared__ int s_stop;
 
-    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nwarps = blockDim.x >> 5, BD = blockDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     const int sub = lane % LPC, grp = lane / LPC;
-    const int gw = blockIdx.x * nwarps + wib, nw_grid = gridDim.x * nwarps;
     const Acc lam = (Acc)a.lambda;
-    const int n_nzr = a.stats->n_nzr, n_nzc = a.stats->n_nzc, n_zr = a.stats->n_zr;
+    const int n_nzr = a.stats->n_nzr, n_nzc = a.stats->n_nzc;
 
-    // ---- prologue: p and f into compacted order; ||p||^2 terms ----
-    for (int q = blockIdx.x * BD + tid; q < n_nzr; q += gridDim.x * BD) stcg(a.pc + q, ldg(a.p12 + __ldg(a.nzr + q)));
-    for (int q = blockIdx.x * BD + tid; q < n_nzc; q += gridDim.x * BD) stcg(a.fc + q, ldcg(a.f12 + __ldg(a.nzc + q)));
-    double ppz = 0.0;  // non-batch, thread 0: this CTA's share of the empty rows' ||p||^2
-    if constexpr (kBatch) {
-        for (int sl = gw; sl < a.ns; sl += nw_grid) {
-            const long long r0 = __ldg(a.sl_rows + sl), r1 = __ldg(a.sl_rows + sl + 1);
-            double t = 0.0;
-            for (long long i = r0 + lane; i < r1; i += 32) {
-                const V2 p = ldg(a.p12 + i);
-                t += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
-            }
-            // The slice's empty rows: a range of the increasing list zr.
-            int lo = 0, hi = n_zr;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if ((long long)__ldg(a.zr + mid) < r0) lo = mid + 1;
-                else hi = mid;
-            }
-            double z = 0.0;
-            for (int k = lo + lane; k < n_zr && (long long)__ldg(a.zr + k) < r1; k += 32) {
-                const V2 p = ldg(a.p12 + __ldg(a.zr + k));
-                z += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
-            }
-            t = warp_sum(t);
-            z = warp_sum(z);
-            if (lane == 0) {
-                a.sl_solve[sl] = SliceSolve{-1, 0, 0.0, 0.0, t};
-                a.pz[sl] = z;
-            }
-        }
-    } else {
-        const long long G = gridDim.x, b = blockIdx.x;
-        const int z0 = (int)(n_zr * b / G), z1 = (int)(n_zr * (b + 1) / G);
-        const long long m0 = (long long)a.Mh * b / G, m1 = (long long)a.Mh * (b + 1) / G;
-        double tz = 0.0, ta = 0.0;
-        for (int z = z0 + tid; z < z1; z += BD) {
-            const V2 p = ldg(a.p12 + __ldg(a.zr + z));
-            tz += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
-        }
-        for (long long i = m0 + tid; i < m1; i += BD) {
-            const V2 p = ldg(a.p12 + i);
-            ta += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
-        }
-        tz = warp_sum(tz);
-        ta = warp_sum(ta);
-        if (lane == 0) s_red[wib] = tz;
-        __syncthreads();
-        if (tid == 0)
-            for (int w = 0; w < nwarps; ++w) ppz += s_red[w];
-        __syncthreads();
-        if (lane == 0) s_red[wib] = ta;
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < nwarps; ++w) t += s_red[w];
-            __stcg(a.partials + 2 * blockIdx.x + 1, t);
-        }
-    }
+    const double ppz = st_prologue<T, kImplicit, kBatch>(a, s_red);  // thread 0: empty rows' ||p||^2
     unsigned nbar = 0;
     if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     if (!kBatch && wib == 0) {
         const double t = grid_total(a.partials, gridDim.x, lane, 1);
         if (lane == 0) s_tpp = t;
     }
-    // On stopping: f back from compacted order (every CTA its share), then return.
-    auto write_back = [&]() {
-        for (int q = blockIdx.x * BD + tid; q < n_nzc; q += gridDim.x * BD) stcg(a.f12 + __ldg(a.nzc + q), ldcg(a.fc + q));
-    };
 
     // A step's loads (U entries per lane and item, lane-strided by W from `first`), then its use.
     auto load_step = [&](auto UC, auto& B, const int32_t* idx, const Val* val, const int (&lo)[R], const int (&hi)[R],
@@ -659,81 +492,11 @@ __global__ void __launch_bounds__(512, 1) sart_compact_kernel(StArgs<T, kImplici
             irm = nirm;
             scm = nscm;
         }
-        if constexpr (!kBatch) {
-            const double t = warp_sum(rr.sum());
-            if (lane == 0) s_red[wib] = t;
-            __syncthreads();
-            if (tid == 0) {
-                double tot = ppz;  // an empty row's residual is its p
-                for (int w = 0; w < nwarps; ++w) tot += s_red[w];
-                __stcg(a.partials + 2 * blockIdx.x, tot);
-            }
-        }
+        if constexpr (!kBatch) st_rr_partial(rr.sum(), ppz, a.partials, s_red);
         if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
 
-        const bool last = k >= a.max_iters;
-        if constexpr (kBatch) {
-            // ---- per-slice stop tests: one CTA per slice, fixed order ----
-            if (last || (k % a.check_every == 0)) {
-                for (int sl = blockIdx.x; sl < a.ns; sl += gridDim.x) {
-                    if (__ldcg(&a.sl_solve[sl].done)) continue;  // uniform over the CTA
-                    double t = 0.0;
-                    for (int q = __ldg(a.qs + sl) + tid; q < __ldg(a.qs + sl + 1); q += BD) t += __ldcg(a.rr + q);
-                    t = warp_sum(t);
-                    if (lane == 0) s_red[wib] = t;
-                    __syncthreads();
-                    if (tid == 0) {
-                        double trr = __ldcg(a.pz + sl);
-                        for (int w = 0; w < nwarps; ++w) trr += s_red[w];
-                        const double tpp = __ldcg(&a.sl_solve[sl].pp);
-                        const bool above = !last && tpp > 0.0 && trr > tpp * a.tol2_hi;
-                        const double rho = (above || !(tpp > 0.0)) ? 0.0 : sqrt(trr / tpp);
-                        if (!above && (last || rho <= a.tol)) {
-                            a.sl_solve[sl] = SliceSolve{k, 1, rho, trr, tpp};
-                            atomicAdd(a.ndone, 1);
-                        }
-                    }
-                    __syncthreads();
-                }
-            }
-            if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
-            if (ld_volatile(a.ndone) >= a.ns) {
-                if (blockIdx.x == 0 && tid == 0) {
-                    a.result->iters = k;
-                    a.result->status = SPLITSART_OK;
-                    a.result->rho = 0.0;
-                    a.result->rr = 0.0;
-                    a.result->pp = 0.0;
-                }
-                write_back();
-                return;
-            }
-        } else if (last || (k % a.check_every == 0)) {
-            if (wib == 0) {
-                const double trr = grid_total(a.partials, gridDim.x, lane, 0);
-                if (lane == 0) {
-                    const double tpp = s_tpp;
-                    int stop = 0;
-                    if (last || !(tpp > 0.0) || trr <= tpp * a.tol2_hi) {
-                        const double rho = tpp > 0.0 ? sqrt(trr / tpp) : 0.0;
-                        stop = (last || rho <= a.tol) ? 1 : 0;
-                        if (stop && blockIdx.x == 0) {
-                            a.result->iters = k;
-                            a.result->status = SPLITSART_OK;
-                            a.result->rho = rho;
-                            a.result->rr = trr;
-                            a.result->pp = tpp;
-                        }
-                    }
-                    s_stop = stop;
-                }
-            }
-            __syncthreads();
-            if (s_stop) {
-                write_back();
-                return;
-            }
-        }
+        const int stop = st_stop_test<T, kImplicit, kBatch>(a, k, s_red, s_tpp, &s_stop, nbar);
+        if (stop != 0) return;  // stopped (f written back), or a barrier wait failed
 
         // ---- back-projection and update: f += lambda (A^T u) / C per compacted column ----
         if (blockIdx.x == 0 && tid == 0) a.ctl->work[0] = 0;  // the forward pass's counter, idle until the barrier
@@ -860,8 +623,6 @@ struct PipeShape {
 template <class T, bool kImplicit, int LPC>
 int launch_pipe(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o, cudaStream_t st) {
     using V2 = typename T::Vec2;
-    using N2 = typename T::KNorm2;
-    using Val = typename Stor<T, kImplicit>::Val;
     constexpr bool kWide = sizeof(V2) == 16;
     using Shape = PipeShape<kImplicit || T::kQuant, kWide>;  // 2-byte codes take registers like the implicit fold
     constexpr int UF = Shape::UF, UB = Shape::UB, R = Shape::R;
@@ -893,51 +654,8 @@ int launch_pipe(splitsart_system* s, const void* p12, void* f12, const splitsart
     int grid = nsm * per_sm;
     if (grid > kMaxCtas) grid = kMaxCtas;
 
-    StArgs<T, kImplicit> a{};
-    a.rp = F.rp;
-    a.ci = F.ci;
-    a.cv = (const Val*)F.cv;
-    a.cp = F.cp;
-    a.ri = F.ri;
-    a.rv = (const Val*)F.rv;
-    a.ir = (const N2*)F.ir;
-    a.ic = (const N2*)F.ic;
-    a.sc = F.sc;
-    a.pc = (V2*)F.pc;
-    a.uc = (V2*)F.uc;
-    a.fc = (V2*)F.fc;
-    a.rr = F.rr;
-    a.qs = F.qs;
-    a.cs = F.cs;
-    a.pz = F.pz;
-    a.p12 = (const V2*)p12;
-    a.f12 = (V2*)f12;
-    a.nzr = s->nzr;
-    a.nzc = s->nzc;
-    a.zr = s->zr;
-    a.stats = s->stats;
-    a.partials = s->partials;
-    a.ctl = s->ctl;
-    a.result = s->result;
-    a.Mh = (int)s->Mh;
-    a.ns = s->ns;
-    a.sl_rows = s->sl_rows;
-    a.sl_solve = s->sl_solve;
-    a.ndone = s->ndone;
-    a.max_iters = o.max_iters;
-    a.check_every = o.check_every > 0 ? o.check_every : 1;
-    a.lambda = o.lambda;
-    a.tol = o.tol;
-    a.tol2_hi = o.tol * o.tol * (1.0 + 1e-12);
-    const double tms = o.timeout_ms > 0 ? o.timeout_ms : 2000.0;
-    a.timeout_ns = (unsigned long long)(tms * 1e6);
-    a.expected = (unsigned)grid + (o.inject_barrier_fault ? 1u : 0u);
-
-    if ((e = cudaMemsetAsync(s->ctl, 0, sizeof(LaunchCtl), st)) != cudaSuccess) return cuda_fail(e, "solve: memset");
-    if ((e = cudaMemsetAsync(s->result, 0xff, sizeof(SolveResultDev), st)) != cudaSuccess)
-        return cuda_fail(e, "solve: memset");
-    if (batch && (e = cudaMemsetAsync(s->ndone, 0, sizeof(int), st)) != cudaSuccess)
-        return cuda_fail(e, "solve: memset");
+    StArgs<T, kImplicit> a = st_args<T, kImplicit>(s, F, p12, f12, o, grid);
+    if ((rc = st_reset(s, st)) != SPLITSART_OK) return rc;
     void* args[] = {&a};
     e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(threads), args, 0, st);
     if (e != cudaSuccess) return cuda_fail(e, "solve: cooperative launch");
@@ -954,6 +672,19 @@ int launch_pipe_lpc(splitsart_system* s, const void* p12, void* f12, const split
 }
 
 }  // namespace
+
+int stream_format(splitsart_system* s, int kind, cudaStream_t st) {
+    FoldStats fs;
+    const int rc = system_host_stats(s, &fs);
+    if (rc) return rc;
+    switch (s->dtype) {
+        case SPLITSART_F64: return build_stream_format<TF64>(s, kind, fs, st);
+        case SPLITSART_F32: return build_stream_format<TF32>(s, kind, fs, st);
+        case SPLITSART_BF16: return build_stream_format<TBF16>(s, kind, fs, st);
+        case SPLITSART_F16: return build_stream_format<TF16>(s, kind, fs, st);
+    }
+    return fail(SPLITSART_ERR_ARG, "solve: unknown value storage");
+}
 
 int run_solve_stream(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o, cudaStream_t st) {
     const bool imp = o.kernel == 6;

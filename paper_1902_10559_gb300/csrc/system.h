@@ -78,6 +78,14 @@ struct StreamFmt {
     int32_t* qs = nullptr;   // [ns + 1] first compacted row of each slice
     int32_t* cs = nullptr;   // [n_nzc] slice of each compacted column
     double* pz = nullptr;    // [ns] ||p||^2 of each slice's empty rows (per launch)
+    // Chunk plans of the ring kernels (ring.cu), made on their first use for a
+    // chunk entry target: chunk c of pass k is rows (k = 0) or columns (k = 1)
+    // [desc[k][c].x, desc[k][c + 1].x), whose entries start at desc[k][c].y.
+    int ring_E = 0;                  // entry target of the plans (0: none yet)
+    int ring_nch[2] = {0, 0};        // chunks per pass
+    int ring_len[2] = {0, 0};        // longest row, longest column
+    int2* ring_desc[2] = {nullptr, nullptr};
+    void* ring_alloc = nullptr;
 };
 
 // Per-slice solve state of a batch launch.
@@ -208,6 +216,10 @@ int run_solve_os(splitsart_system* s, const void* p12, void* f12, const splitsar
                  const splitsart_os_opts& os, cudaStream_t st);
 int run_solve_cgls(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o, cudaStream_t st);
 int run_solve_stream(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o, cudaStream_t st);
+// Defined in stream.cu: build compacted format `kind` (0 explicit, 1 implicit) of s once.
+int stream_format(splitsart_system* s, int kind, cudaStream_t st);
+// Defined in ring.cu: solve kernels 7 and 8.
+int run_solve_ring(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o, cudaStream_t st);
 // Defined in fold.cu: the implicit fold of the half rows (entry d of half row i
 // at hrp[i] + d, in the fold's merged column order), as global folded columns
 // with A1's sign in bit 31 and FP64 or FP32 lengths.

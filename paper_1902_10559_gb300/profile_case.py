@@ -29,6 +29,7 @@ def main():
     ap.add_argument("--kernel", type=int, default=0)
     ap.add_argument("--lpc", type=int, default=4)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=0, help="kernels 7 and 8: chunk entry target (0 = library default)")
     ap.add_argument("--nrhs", type=int, default=64)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--rc", type=int, default=0, help="multi: right-hand sides per CTA (0 = library choice)")
@@ -54,7 +55,7 @@ def main():
         p12 = torch.empty(sysm.Mh, 2, device=dev)
         ss.fold_rhs(sysm, p, p12)
         f12 = torch.zeros(sysm.Nh, 2, device=dev)
-        opts = ss.solve_opts(args.iters, 0.8, kernel=args.kernel, lanes_per_col=args.lpc,
+        opts = ss.solve_opts(args.iters, 0.8, kernel=args.kernel, lanes_per_col=args.lpc, tile_entries=args.tile,
                              block_threads=args.threads)
         for _ in range(2):
             f12.zero_()

@@ -343,7 +343,9 @@ def solve_opts(max_iters: int, lam: float, tol: float = 0.0, check_every: int = 
                inject_barrier_fault: bool = False, kernel: int = 0, tile_entries: int = 0,
                row_weight: int = 0) -> SolveOpts:
     """Solve options (splitsart_solve_opts). kernel: 0 = library choice, 1 = CTA-wide tiles,
-    2 = shared-memory resident, 3 = row streaming, 4 = per-warp bulk copies."""
+    2 = shared-memory resident, 3 = row streaming, 4 = per-warp bulk copies, 5/6 = row streaming in
+    compacted order (explicit/implicit fold), 7/8 = the same fed by a producer warp through a
+    shared-memory ring (explicit/implicit fold)."""
     return SolveOpts(max_iters, lam, tol, check_every, block_threads, ctas_per_sm, lanes_per_col, kernel, timeout_ms,
                      int(inject_barrier_fault), tile_entries, row_weight)
 

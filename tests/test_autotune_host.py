@@ -52,9 +52,16 @@ def test_candidates_are_valid_launch_shapes(dtype, nslices):
     seen = set()
     for c in cands:
         assert keys <= set(c)
-        assert c["kernel"] in (1, 2, 3, 4, 5)  # never 6: the implicit fold changes the rounding
+        seen.add(tuple(sorted(c.items())))
+        assert c["kernel"] in (1, 2, 3, 4, 5, 7)  # never 6 or 8: the implicit fold changes the rounding
         assert c["lanes_per_col"] in VALID_LPC
         bt = c["block_threads"]
+        if c["kernel"] == 7:  # a fixed CTA shape (producer warp + consumers); tile_entries = chunk target
+            assert bt == 0 and c["lanes_per_col"] in (4, 8)
+            te = c["tile_entries"]
+            assert te == 0 or (te % 1024 == 0 and 1024 <= te <= 16384)
+            ss.solve_opts(10, 1.0, **c)
+            continue
         assert bt % 32 == 0 and 64 <= bt <= 1024
         if c["kernel"] in (2, 3, 5):
             assert bt <= 512
@@ -73,7 +80,6 @@ def test_candidates_are_valid_launch_shapes(dtype, nslices):
             assert nslices == 1  # the resident kernel has no per-slice stop tests
         # All fields are plain keyword arguments of solve_opts.
         ss.solve_opts(10, 1.0, **c)
-        seen.add(tuple(sorted(c.items())))
     assert len(seen) == len(cands)  # no candidate is timed twice
 
 

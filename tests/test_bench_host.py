@@ -43,6 +43,7 @@ def test_committed_profiles_match_their_kernel_sources():
     for name, src in (("sart_resident_realistic_fp32.txt", bench.KERNEL_SRC),
                       ("sart_rows_batch_fp32.txt", bench.KERNEL_SRC),
                       ("sart_compact_batch_fp32.txt", bench.STREAM_SRC),
+                      ("sart_ring_batch_fp32.txt", bench.RING_SRC),
                       ("sart_multi_tiny64_fp32.txt", bench.MULTI_SRC),
                       ("sart_multi_tiny64_bf16.txt", bench.MULTI_SRC)):
         assert bench.profile_traffic(name, src, algorithmic_bytes=1.0) is not None, name
