@@ -312,8 +312,9 @@ typedef struct splitsart_solve_opts {
                               per CTA one producer warp copies chunks of rows (columns) with bulk asynchronous
                               copies and the other warps only gather and sum; they return kernel 5's and 6's
                               f bit for bit at equal lanes_per_col. tile_entries is their chunk entry target
-                              (0 = about 48 KB of entries per chunk); a chunk must fit in the ring (about
-                              225 KB of shared memory), else SPLITSART_ERR_ARG. block_threads and
+                              (0 = 4096 for 12-byte entries, 3072 for 8-byte ones, else about 48 KB of
+                              entries); a chunk must fit in the ring (about 225 KB of shared memory; 160 KB
+                              for 8-byte entries, leaving the rest to L1), else SPLITSART_ERR_ARG. block_threads and
                               ctas_per_sm are not used (one CTA per SM). Their first use also makes the chunk
                               plans (one synchronisation) and keeps them with the system */
     double timeout_ms;     /* limit of each grid-barrier wait (kernels 4, 7, 8: also of each wait on a bulk copy

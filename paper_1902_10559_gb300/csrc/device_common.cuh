@@ -164,12 +164,14 @@ struct LaunchCtl {
 //   needs no round trip; no separate fence);
 // - it then waits until the count reaches `target`, which is
 //   expected x (barrier index + 1).
-// The wait has a wall-clock limit and a spin cap. If either runs out, the wait
-// records SPLITSART_ERR_TIMEOUT in ctl->err and stops waiting. `expected` is
-// normally gridDim.x; a test passes gridDim.x + 1 to make the wait run out on
-// purpose.
-// Returns false, for every thread of the CTA, if any CTA has recorded an
-// error. The caller must then return.
+// The wait has a wall-clock limit (checked every 64 polls) and a spin cap. If
+// either runs out, the wait records SPLITSART_ERR_TIMEOUT in ctl->err and
+// stops waiting. `expected` is normally gridDim.x; a test passes gridDim.x + 1
+// to make the wait run out on purpose.
+// Returns false, for every thread of the CTA, if this CTA saw an error
+// recorded by any CTA while it waited. The caller must then return. (A CTA
+// that passes a barrier just as another records an error learns of it at the
+// next barrier, which the failed CTA never reaches.)
 __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -182,23 +184,28 @@ __device__ __forceinline__ bool grid_sync(LaunchCtl* ctl, unsigned target, unsig
         // The release orders this CTA's earlier writes: the CTA barrier above puts
         // them before this thread's release, and release is cumulative.
         red_release_add(&ctl->bar_count, 1u);
-        if (ld_acquire_gpu(&ctl->bar_count) < target) {
-            const unsigned long long t0 = global_ns();
-            const unsigned long long max_spins = timeout_ns / 32ull + (1ull << 20);
-            unsigned long long spins = 0;
-            while (ld_acquire_gpu(&ctl->bar_count) < target) {
-                if (ld_volatile(&ctl->err) != 0) { ok = 0; break; }
-                if (global_ns() - t0 > timeout_ns || ++spins > max_spins) {
-                    if (atomicCAS(&ctl->err, 0, SPLITSART_ERR_TIMEOUT) == 0) ctl->err_where = where;
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(20);
+        const unsigned long long max_spins = timeout_ns / 32ull + (1ull << 20);
+        unsigned long long t0 = 0, spins = 0;
+        for (;;) {
+            // The error flag is read first, with a plain load, so that it travels with the
+            // acquire load of the count: one round trip per poll.
+            const int err = ld_volatile(&ctl->err);
+            const unsigned count = ld_acquire_gpu(&ctl->bar_count);
+            if (err != 0) {
+                ok = 0;
+                break;
             }
+            if (count >= target) break;
+            if (spins == 0) t0 = global_ns();
+            if (++spins > max_spins || ((spins & 63) == 0 && global_ns() - t0 > timeout_ns)) {
+                if (atomicCAS(&ctl->err, 0, SPLITSART_ERR_TIMEOUT) == 0) ctl->err_where = where;
+                ok = 0;
+                break;
+            }
+            __nanosleep(20);
         }
-        // The acquire loads above, and the CTA barrier below, put the other CTAs'
-        // writes before every later load of this CTA.
-        if (ld_volatile(&ctl->err) != 0) ok = 0;
+        // The acquire load, and the CTA barrier below, put the other CTAs' writes
+        // before every later load of this CTA.
         s_ok = ok;
     }
     __syncthreads();

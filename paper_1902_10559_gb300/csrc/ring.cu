@@ -551,14 +551,30 @@ struct RingShape {
     static constexpr int UB = kWide ? 2 : 4;
 };
 
-// Chunk entry target when tile_entries is 0: about 48 KB of indices and values
-// per chunk (4096 entries of the explicit FP32 fold, 6144 of 8-byte entries).
-// On the 256-slice batch the explicit FP32 fold ran 812/536/507/521 ms at
-// 1024/2048/4096/6144 entries, the implicit one 827/514/483/455 ms.
+// Chunk entry target when tile_entries is 0, and the ring's size. On the
+// 256-slice batch (200 iterations, lanes_per_col 4; ms for chunks of
+// 2048/4096 entries explicit FP32, 3072/6144 for the 8-byte forms):
+//   ring          explicit FP32   implicit FP32   BF16 codes
+//   228 KB        539 / 510       497 / 458       501 / 462
+//   164 KB        532 / 566       441 / 454       439 / 452
+//   132 KB        564 / 711       453 / 560       451 / 557
+// so the explicit FP32 fold keeps the full ring with 4096-entry chunks (about
+// 48 KB), and 8-byte entries take a 164 KB ring with 3072-entry chunks: the
+// shared memory given back becomes L1, where their gathers, 1.5 times as many
+// per byte streamed, hit more often. Other widths take about 48 KB chunks.
 template <class Val>
 constexpr int ring_default_E() {
-    const int e = 49152 / (4 + (int)sizeof(Val)) / 1024 * 1024;
+    constexpr int entry = 4 + (int)sizeof(Val);
+    if (entry == 8) return 3072;
+    const int e = 49152 / entry / 1024 * 1024;
     return e < 1024 ? 1024 : e;
+}
+// The whole shared memory of a CTA (ring, barriers and headers, static
+// variables and the 1 KB the SM reserves per CTA) stays within this, so that
+// the rest of the SM's 256 KB array serves as L1.
+template <class Val>
+constexpr long long ring_smem_cap() {
+    return 4 + sizeof(Val) == 8 ? 164LL * 1024 : (1LL << 40);
 }
 
 // The chunk plans of format F (kind 0 explicit, 1 implicit) for entry target
@@ -635,7 +651,8 @@ int launch_ring(splitsart_system* s, const void* p12, void* f12, const splitsart
                              : (const void*)sart_ring_kernel<T, kImplicit, false, LPC, UF, UB, R, W>;
     cudaFuncAttributes fa{};
     if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return cuda_fail(e, "solve: kernel attributes");
-    const long long ring = ((long long)optin - (long long)fa.sharedSizeBytes - kRingPrefix) / 128 * 128;
+    const long long fixed = (long long)fa.sharedSizeBytes + kRingPrefix;
+    const long long ring = std::min((long long)optin - fixed, ring_smem_cap<Val>() - 1024 - fixed) / 128 * 128;
     // The largest chunk: at most E + 8 pointers and E + L + 8 entries staged (L the longest row or column).
     long long chunk = 0;
     for (int k = 0; k < 2; ++k)
