@@ -325,6 +325,10 @@ typedef struct splitsart_solve_opts {
     int32_t row_weight;    /* kernel 2: when rows are dealt to CTAs, each row weighs this many entries more than
                               its length (a row's fixed cost). 0 = default: the heaviest of 240, 160, 80, 40, 0
                               whose plan fits in shared memory; a value that does not fit falls back the same way */
+    int32_t lanes_per_row; /* kernels 7 and 8: forward-pass lanes per row, 8, 16 or 32; 0 = default. At 32 a row
+                              is summed by the whole warp in kernels 5's and 6's order (bitwise their f); fewer
+                              lanes put 32 / lanes_per_row rows of a warp in flight at once, with the row's sum
+                              lane-strided over its lanes and reduced by their shuffle tree (another fixed order) */
 } splitsart_solve_opts;
 
 /*

@@ -133,9 +133,10 @@ __device__ __forceinline__ void ring_abort(LaunchCtl* ctl, int where, volatile i
     *abort = 1;
 }
 
-// UF, UB: entries in flight per lane and item (forward, back); R: rows per
-// consumer step (columns per lane group); W: consumer warps (the CTA has W + 1).
-template <class T, bool kImplicit, bool kBatch, int LPC, int UF, int UB, int R, int W>
+// LPC, LPR: lanes per column (back pass) and per row (forward pass); UF, UB:
+// entries in flight per lane and item (forward, back); R: items per lane group
+// and step; W: consumer warps (the CTA has W + 1).
+template <class T, bool kImplicit, bool kBatch, int LPC, int LPR, int UF, int UB, int R, int W>
 __global__ void __launch_bounds__(32 * (W + 1), 1) sart_ring_kernel(RingArgs<T, kImplicit> ra) {
     using Acc = typename T::Acc;
     using V2 = typename T::Vec2;
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) sart_ring_kernel(RingArgs<T, 
     constexpr int kColStep = R * kGroups;  // columns per consumer step
     constexpr int kW = W;
     constexpr unsigned kFull = 0xffffffffu;
-    static_assert(kColStep <= 32, "a lane holds the data of one column of a step");
+    static_assert(kColStep <= 32 && R * (32 / LPR) <= 32, "a lane holds the data of one item of a step");
     const StArgs<T, kImplicit>& a = ra.st;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
@@ -318,8 +319,13 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) sart_ring_kernel(RingArgs<T, 
         ++kc;
     };
 
-    // Consumer, forward: r = p - A f and u = r / R for the rows of its chunks.
+    // Consumer, forward: r = p - A f and u = r / R for the rows of its chunks. A step takes
+    // kRowStep rows: item g of lane group grpr (LPR lanes) is row cb + g kRG + grpr. With
+    // LPR = 32 a step is R rows, each summed by the whole warp as in kernels 5 and 6.
     auto consume_rows = [&](SqAcc<Acc>& rr) __attribute__((always_inline)) -> bool {
+        constexpr int kRG = 32 / LPR;
+        constexpr int kRowStep = R * kRG;
+        const int subr = lane % LPR, grpr = lane / LPR;
         for (;;) {
             unsigned slot;
             RingHdr h;
@@ -331,21 +337,23 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) sart_ring_kernel(RingArgs<T, 
             const int32_t* sp = reinterpret_cast<const int32_t*>(ring + h.off);
             const int32_t* sidx = sp + h.nqa;
             const Val* sval = reinterpret_cast<const Val*>(sidx + h.nea);
-            const int nq = h.q1 - h.q0, ngr = (nq + R - 1) / R;
-            for (int gi = (wib - rot + kW) % kW; gi < ngr; gi += kW) {
-                const int j = gi * R;
+            const int nq = h.q1 - h.q0, nst = (nq + kRowStep - 1) / kRowStep;
+            for (int si = (wib - rot + kW) % kW; si < nst; si += kW) {
+                const int cb = si * kRowStep;
                 int lo[R], hi[R], len = 0;
 #pragma unroll
                 for (int g = 0; g < R; ++g) {
-                    const bool has = j + g < nq;
-                    const int r = h.q0 - h.q0a + j + g;
+                    const int krow = cb + g * kRG + grpr;
+                    const bool has = krow < nq;
+                    const int r = h.q0 - h.q0a + krow;
                     lo[g] = has ? sp[r] - h.e0a : 0;
                     hi[g] = has ? sp[r + 1] - h.e0a : 0;
                     len = max(len, hi[g] - lo[g]);
                 }
-                // Lane g < R finishes row j + g; its p, 1/R (and scale) load during the sums.
-                const int qr = h.q0 + j + lane;
-                const bool mine = lane < R && j + lane < nq;
+                if constexpr (LPR < 32) len = (int)__reduce_max_sync(kFull, (unsigned)len);
+                // Lane t < kRowStep finishes row cb + t; its p, 1/R (and scale) load during the sums.
+                const int qr = h.q0 + cb + lane;
+                const bool mine = lane < kRowStep && cb + lane < nq;
                 V2 pm{};
                 N2 irm{};
                 float2 scm{1.f, 1.f};
@@ -359,14 +367,14 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) sart_ring_kernel(RingArgs<T, 
                 for (int g = 0; g < R; ++g) s1[g] = s2[g] = 0;
                 // A round: the gathers of up to UF entries per lane and row in flight together; the
                 // values are read from shared memory again once the gathers are back.
-                for (int off = 0; off < len; off += 32 * UF) {
+                for (int off = 0; off < len; off += LPR * UF) {
                     int32_t ia[R][UF];
                     V2 gv[R][UF];
 #pragma unroll
                     for (int g = 0; g < R; ++g)
 #pragma unroll
                         for (int u = 0; u < UF; ++u) {
-                            const int e = lo[g] + off + lane + 32 * u;
+                            const int e = lo[g] + off + subr + LPR * u;
                             if (e < hi[g]) {
                                 ia[g][u] = sidx[e];
                                 gv[g][u] = ldca(a.fc + St::col(ia[g][u]));
@@ -376,7 +384,7 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) sart_ring_kernel(RingArgs<T, 
                     for (int g = 0; g < R; ++g)
 #pragma unroll
                         for (int u = 0; u < UF; ++u) {
-                            const int e = lo[g] + off + lane + 32 * u;
+                            const int e = lo[g] + off + subr + LPR * u;
                             if (e < hi[g]) {
                                 int jj;
                                 Acc v1, v2;
@@ -388,17 +396,21 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) sart_ring_kernel(RingArgs<T, 
                 }
 #pragma unroll
                 for (int g = 0; g < R; ++g) {
-                    s1[g] = warp_sum(s1[g]);
-                    s2[g] = warp_sum(s2[g]);
+                    s1[g] = warp_sum(s1[g], LPR);
+                    s2[g] = warp_sum(s2[g], LPR);
+                }
+                // Row cb + t was item t / kRG of lane group t mod kRG.
+                const int src = (mine ? lane % kRG : 0) * LPR, item = mine ? lane / kRG : 0;
+                Acc t1 = 0, t2 = 0;
+#pragma unroll
+                for (int g = 0; g < R; ++g) {
+                    const Acc z1 = __shfl_sync(kFull, s1[g], src), z2 = __shfl_sync(kFull, s2[g], src);
+                    if (item == g) {
+                        t1 = z1;
+                        t2 = z2;
+                    }
                 }
                 if (mine) {
-                    Acc t1 = s1[0], t2 = s2[0];
-#pragma unroll
-                    for (int g = 1; g < R; ++g)
-                        if (lane == g) {
-                            t1 = s1[g];
-                            t2 = s2[g];
-                        }
                     if constexpr (T::kQuant) {  // codes times the row's scale; 1/R already holds it for u
                         t1 *= scm.x;
                         t2 *= scm.y;
@@ -409,7 +421,7 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) sart_ring_kernel(RingArgs<T, 
                     else rr.add(r1, r2);
                 }
             }
-            rot = (rot + ngr) % kW;
+            rot = (rot + nst) % kW;
             release(slot);
         }
     };
@@ -536,18 +548,20 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) sart_ring_kernel(RingArgs<T, 
     }
 }
 
-// Consumer step shape: W consumer warps (the CTA has W + 1), R items per step,
-// UF (UB) entries in flight per lane and item in the forward (back) pass.
-// kWide: FP64 vectors. On the 256-slice batch (FP32, 200 iterations, 4096
-// entries per chunk) 23 warps with one row per step ran 532 ms explicit and
-// 477 ms implicit (6144 entries per chunk), against 558/493 ms for 15 warps
-// with two rows, 546/645 ms for 23 warps with two rows and 532/491 ms for 31
-// warps with one row.
-template <bool kWide>
+// Consumer step shape for LPR lanes per row: W consumer warps (the CTA has
+// W + 1), R items per lane group and step, UF (UB) entries in flight per lane
+// and item in the forward (back) pass. kWide: FP64 vectors. On the 256-slice
+// batch (FP32, 200 iterations, 4096 entries per chunk, LPR = 32) 23 warps with
+// one row per step ran 532 ms explicit and 477 ms implicit (6144 entries per
+// chunk), against 558/493 ms for 15 warps with two rows, 546/645 ms for 23
+// warps with two rows and 532/491 ms for 31 warps with one row.
+constexpr int kRingDefaultLPR = 32;  // forward-pass lanes per row when lanes_per_row is 0
+
+template <bool kWide, int LPR>
 struct RingShape {
     static constexpr int W = kWide ? 15 : 23;
     static constexpr int R = kWide ? 2 : 1;
-    static constexpr int UF = kWide ? 2 : 4;
+    static constexpr int UF = (kWide ? 2 : 4) * (LPR == 32 ? 1 : 2);
     static constexpr int UB = kWide ? 2 : 4;
 };
 
@@ -625,11 +639,11 @@ int ring_plans(splitsart_system* s, StreamFmt& F, int kind, int E, cudaStream_t 
     return SPLITSART_OK;
 }
 
-template <class T, bool kImplicit, int LPC>
+template <class T, bool kImplicit, int LPC, int LPR>
 int launch_ring(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o, cudaStream_t st) {
     using V2 = typename T::Vec2;
     using Val = typename Stor<T, kImplicit>::Val;
-    using Shape = RingShape<sizeof(V2) == 16>;
+    using Shape = RingShape<sizeof(V2) == 16, LPR>;
     constexpr int R = Shape::R, UF = Shape::UF, UB = Shape::UB, W = Shape::W;
     constexpr int threads = 32 * (W + 1);
     const int kind = kImplicit ? 1 : 0;
@@ -647,8 +661,8 @@ int launch_ring(splitsart_system* s, const void* p12, void* f12, const splitsart
     const int E = o.tile_entries > 0 ? o.tile_entries : ring_default_E<Val>();
     if ((rc = ring_plans(s, F, kind, E, st)) != SPLITSART_OK) return rc;
     const bool batch = s->ns > 1;
-    const void* kern = batch ? (const void*)sart_ring_kernel<T, kImplicit, true, LPC, UF, UB, R, W>
-                             : (const void*)sart_ring_kernel<T, kImplicit, false, LPC, UF, UB, R, W>;
+    const void* kern = batch ? (const void*)sart_ring_kernel<T, kImplicit, true, LPC, LPR, UF, UB, R, W>
+                             : (const void*)sart_ring_kernel<T, kImplicit, false, LPC, LPR, UF, UB, R, W>;
     cudaFuncAttributes fa{};
     if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return cuda_fail(e, "solve: kernel attributes");
     const long long fixed = (long long)fa.sharedSizeBytes + kRingPrefix;
@@ -686,11 +700,21 @@ int launch_ring(splitsart_system* s, const void* p12, void* f12, const splitsart
     return SPLITSART_OK;
 }
 
+template <class T, bool kImplicit, int LPC>
+int launch_ring_lpr(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o, cudaStream_t st) {
+    switch (o.lanes_per_row > 0 ? o.lanes_per_row : kRingDefaultLPR) {
+        case 8: return launch_ring<T, kImplicit, LPC, 8>(s, p12, f12, o, st);
+        case 16: return launch_ring<T, kImplicit, LPC, 16>(s, p12, f12, o, st);
+        case 32: return launch_ring<T, kImplicit, LPC, 32>(s, p12, f12, o, st);
+    }
+    return fail(SPLITSART_ERR_ARG, "solve: kernels 7 and 8 take lanes_per_row 8, 16 or 32");
+}
+
 template <class T, bool kImplicit>
 int launch_ring_lpc(splitsart_system* s, const void* p12, void* f12, const splitsart_solve_opts& o, cudaStream_t st) {
     switch (o.lanes_per_col > 0 ? o.lanes_per_col : 4) {
-        case 4: return launch_ring<T, kImplicit, 4>(s, p12, f12, o, st);
-        case 8: return launch_ring<T, kImplicit, 8>(s, p12, f12, o, st);
+        case 4: return launch_ring_lpr<T, kImplicit, 4>(s, p12, f12, o, st);
+        case 8: return launch_ring_lpr<T, kImplicit, 8>(s, p12, f12, o, st);
     }
     return fail(SPLITSART_ERR_ARG, "solve: kernels 7 and 8 take lanes_per_col 4 or 8");
 }

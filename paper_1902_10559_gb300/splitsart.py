@@ -46,7 +46,7 @@ class SolveOpts(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int32), ("lanes_per_col", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("timeout_ms", ctypes.c_double),
                 ("inject_barrier_fault", ctypes.c_int32), ("tile_entries", ctypes.c_int32),
-                ("row_weight", ctypes.c_int32)]
+                ("row_weight", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32)]
 
 
 class OsOpts(ctypes.Structure):
@@ -341,13 +341,13 @@ def project(system: System, f, p, layout: int = LAYOUT_SNAKE, stream=None) -> No
 def solve_opts(max_iters: int, lam: float, tol: float = 0.0, check_every: int = 1, block_threads: int = 0,
                ctas_per_sm: int = 0, lanes_per_col: int = 0, timeout_ms: float = 0.0,
                inject_barrier_fault: bool = False, kernel: int = 0, tile_entries: int = 0,
-               row_weight: int = 0) -> SolveOpts:
+               row_weight: int = 0, lanes_per_row: int = 0) -> SolveOpts:
     """Solve options (splitsart_solve_opts). kernel: 0 = library choice, 1 = CTA-wide tiles,
     2 = shared-memory resident, 3 = row streaming, 4 = per-warp bulk copies, 5/6 = row streaming in
     compacted order (explicit/implicit fold), 7/8 = the same fed by a producer warp through a
     shared-memory ring (explicit/implicit fold)."""
     return SolveOpts(max_iters, lam, tol, check_every, block_threads, ctas_per_sm, lanes_per_col, kernel, timeout_ms,
-                     int(inject_barrier_fault), tile_entries, row_weight)
+                     int(inject_barrier_fault), tile_entries, row_weight, lanes_per_row)
 
 
 def solve(system: System, p12, f12, opts: SolveOpts, stream=None) -> None:

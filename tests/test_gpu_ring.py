@@ -5,7 +5,8 @@ Kernels 7 (explicit fold) and 8 (implicit fold) run the iteration of kernels
 per-column summation order, so they must return those kernels' iterates
 bit for bit at equal lanes per column, whatever the chunk size. Pins:
 - against the oracle, element by element (1e-10 FP64, 1e-4 FP32), on a slice
-  and on a batch with the per-slice stopping rule;
+  and on a batch with the per-slice stopping rule, with the whole warp on a row
+  and with 8 or 16 lanes per row (another fixed summation order);
 - bitwise against kernels 5 and 6 on a batch large enough that every CTA
   takes many chunks (the producer's bound loads cross several groups of 32
   and the ring wraps), in FP64, FP32, BF16 and FP16, at several chunk sizes;
@@ -71,6 +72,22 @@ def test_tiny_matches_oracle(ss, tiny, kernel, dt, tol, tile):
 
 
 @pytest.mark.parametrize("kernel", [7, 8])
+@pytest.mark.parametrize("dt,tol", [("f64", 1e-10), ("f32", 1e-4)])
+@pytest.mark.parametrize("lpr", [8, 16])
+def test_lanes_per_row_match_oracle(ss, tiny, kernel, dt, tol, lpr):
+    """Fewer lanes per row sum a row in another fixed order: the oracle judges them at the stated tolerance."""
+    A, p, A1, A2, p1, p2 = tiny
+    sysm = ss.fold_system(ss.make_geometry(TINY), ss.DTYPE_NAMES[dt])
+    ref = osart.split_sart(A1, A2, p1, p2, 1.0, 60)
+    infos, f12, f = solve(ss, sysm, p, 60, 1.0, kernel=kernel, lanes_per_row=lpr, tile_entries=1024)
+    assert infos[0]["iters"] == 60 and infos[0]["status"] == 0
+    close(f, osplit.recombine(ref["f1"], ref["f2"]), tol, f"kernel {kernel} ({dt}, {lpr} lanes per row)")
+    close_scalar(infos[0]["rho"], ref["rho"], tol, "rho")
+    _, f12b, _ = solve(ss, sysm, p, 60, 1.0, kernel=kernel, lanes_per_row=lpr, tile_entries=4096)
+    assert np.array_equal(f12, f12b)  # the order is fixed: the chunk size does not change it
+
+
+@pytest.mark.parametrize("kernel", [7, 8])
 def test_stopping_rule(ss, tiny, kernel):
     A, p, A1, A2, p1, p2 = tiny
     sysm = ss.fold_system(ss.make_geometry(TINY), ss.F64)
@@ -84,8 +101,8 @@ def test_stopping_rule(ss, tiny, kernel):
     assert infos[0]["iters"] == 0
 
 
-@pytest.mark.parametrize("kernel", [7, 8])
-def test_batch_matches_oracle_and_stops_per_slice(ss, kernel):
+@pytest.mark.parametrize("kernel,lpr", [(7, 32), (8, 32), (7, 8), (8, 16)])
+def test_batch_matches_oracle_and_stops_per_slice(ss, kernel, lpr):
     from tests.test_gpu_batch import SMALL
     batch = ss.fold_batch([ss.make_geometry(g) for g in SMALL], ss.F64)
     off = ss.system_slices(batch)
@@ -99,7 +116,7 @@ def test_batch_matches_oracle_and_stops_per_slice(ss, kernel):
     p = np.concatenate([c[0] for c in cases])
     hists = [osart.split_sart(c[1], c[2], c[3], c[4], 1.0, 60, record=True)["rho_hist"] for c in cases]
     tol = float(np.median([h[25] for h in hists]))
-    infos, f12, f = solve(ss, batch, p, 60, 1.0, tol=tol, kernel=kernel, tile_entries=1024)
+    infos, f12, f = solve(ss, batch, p, 60, 1.0, tol=tol, kernel=kernel, tile_entries=1024, lanes_per_row=lpr)
     for k, c in enumerate(cases):
         ref = osart.split_sart(c[1], c[2], c[3], c[4], 1.0, 60, tol=tol)
         assert infos[k]["iters"] == ref["iters"], (k, infos[k], ref["iters"])
@@ -187,6 +204,9 @@ def test_chunk_larger_than_the_ring_is_refused(ss):
     assert e.value.code == ss.ERR_ARG and "ring" in str(e.value)
     ss.solve(sysm, p12, f12, ss.solve_opts(3, 1.0, kernel=5))  # the row-streaming kernel takes it
     assert ss.solve_result(sysm)["status"] == 0
+    with pytest.raises(ss.SplitSartError) as e:
+        ss.solve(sysm, p12, f12, ss.solve_opts(3, 1.0, kernel=7, lanes_per_row=4))
+    assert e.value.code == ss.ERR_ARG
 
 
 @pytest.mark.parametrize("kernel", [7, 8])
