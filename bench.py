@@ -600,7 +600,8 @@ class Multi(Realistic):
         self.infobuf = torch.zeros(self.NRHS * ctypes.sizeof(ss.SolveInfo), dtype=torch.uint8, device=dev)
         ss.fold_rhs(self.vec, self.p, self.p12.view(-1, 2))
         self.tuned = autotune.tune_multi(self.system, self.p12, self.f12)
-        self.opts = ss.solve_opts(self.iters, self.lam, block_threads=self.tuned["block_threads"])
+        self.opts = ss.solve_opts(self.iters, self.lam, block_threads=self.tuned["block_threads"],
+                                  lanes_per_row=self.tuned.get("lanes_per_row", 0))
         self.launches = FOLD_LAUNCHES + 3
 
     def step(self, ss, p_in, f_out, layout, ev=None):
@@ -689,7 +690,8 @@ class Precision(Multi):
         out = {}
         for name, (sysm, tuned) in self.forms.items():
             f12 = torch.zeros_like(self.f12)
-            opts = ss.solve_opts(self.MAX_ITERS, self.lam, self.TOL, block_threads=tuned["block_threads"])
+            opts = ss.solve_opts(self.MAX_ITERS, self.lam, self.TOL, block_threads=tuned["block_threads"],
+                                 lanes_per_row=tuned.get("lanes_per_row", 0))
             ts = []
             for _ in range(3):
                 f12.zero_()
@@ -716,7 +718,8 @@ class Precision(Multi):
             # 500 iterations, for the distance between forms.
             f12 = torch.zeros_like(self.f12)
             ss.solve_multi(sysm, self.p12, f12, ss.solve_opts(self.iters, self.lam,
-                                                              block_threads=tuned["block_threads"]),
+                                                              block_threads=tuned["block_threads"],
+                                                              lanes_per_row=tuned.get("lanes_per_row", 0)),
                            self.infobuf, rhs_per_cta=tuned["rhs_per_cta"])
             img = torch.empty(self.NRHS * self.g.N, device=f12.device)
             ss.recombine(self.vec, f12.view(-1, 2), img, layout=ss.LAYOUT_IMAGE)

@@ -325,10 +325,12 @@ typedef struct splitsart_solve_opts {
     int32_t row_weight;    /* kernel 2: when rows are dealt to CTAs, each row weighs this many entries more than
                               its length (a row's fixed cost). 0 = default: the heaviest of 240, 160, 80, 40, 0
                               whose plan fits in shared memory; a value that does not fit falls back the same way */
-    int32_t lanes_per_row; /* kernels 7 and 8: forward-pass lanes per row, 8, 16 or 32; 0 = default. At 32 a row
-                              is summed by the whole warp in kernels 5's and 6's order (bitwise their f); fewer
+    int32_t lanes_per_row; /* kernels 7 and 8: forward-pass lanes per row, 8, 16 or 32; 0 = default (32). At 32 a
+                              row is summed by the whole warp in kernels 5's and 6's order (bitwise their f); fewer
                               lanes put 32 / lanes_per_row rows of a warp in flight at once, with the row's sum
-                              lane-strided over its lanes and reduced by their shuffle tree (another fixed order) */
+                              lane-strided over its lanes and reduced by their shuffle tree (another fixed order).
+                              splitsart_solve_multi: lanes per (row or column, right-hand side), 2, 4 or 8 with
+                              rhs_per_cta x lanes_per_row <= 32; 0 = default (2) */
 } splitsart_solve_opts;
 
 /*
@@ -548,6 +550,9 @@ int splitsart_solve_static(int64_t Mh, int64_t Nh, const int32_t* rp_dev, const 
  * - An iteration touches no global memory, so the launch needs no grid-wide
  *   barrier.
  * - opts->block_threads: a multiple of 32 in [32, 1024] (0 = 512).
+ * - opts->lanes_per_row: lanes per (row or column, right-hand side), 2, 4 or
+ *   8 (0 = 2); a warp sums 32 / (rhs_per_cta x lanes_per_row) rows at once.
+ *   The summation order depends on it (a fixed order for each value).
  * - The system must be a single slice small enough for shared memory.
  *   Otherwise SPLITSART_ERR_ARG: use splitsart_solve per right-hand side.
  * Arguments:

@@ -9,7 +9,8 @@ $SPLITSART_TUNE_CACHE, or ~/.cache/splitsart/tune.json.
   per warp or through a producer warp's shared-memory ring, or per-warp
   bulk-staged streaming), tile entries per CTA (chunk entries of the ring),
   lanes per column in the back-projection, threads per CTA.
-- Multi-right-hand-side solve: right-hand sides per CTA, threads per CTA.
+- Multi-right-hand-side solve: right-hand sides per CTA, threads per CTA,
+  lanes per row and right-hand side.
 
 The tuner only chooses among launch shapes of the same arithmetic, so every
 choice gives a result within rounding of every other.
@@ -132,7 +133,8 @@ def tune_solve(system: ss.System, p12, f12, iters: int = 10, use_cache: bool = T
 
 
 def tune_multi(system: ss.System, p12, f12, iters: int = 10, use_cache: bool = True) -> dict:
-    """Return the fastest (rhs_per_cta, block_threads) for solve_multi on this system and right-hand-side count."""
+    """Return the fastest (rhs_per_cta, block_threads, lanes_per_row) for solve_multi on this system and
+    right-hand-side count (lanes_per_row: lanes per row and right-hand side, 2, 4 or 8)."""
     import torch
     nrhs = p12.shape[0]
     key = f"multi|{nrhs}|" + problem_class(system)
@@ -145,25 +147,29 @@ def tune_multi(system: ss.System, p12, f12, iters: int = 10, use_cache: bool = T
         best, best_t = None, float("inf")
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for rc in (1, 2, 4, 8, 16):
-            for bt in (128, 256, 512, 1024):
-                try:
-                    ts = []
-                    for r in range(3):
-                        f12.copy_(f0)
-                        ev0.record()
-                        ss.solve_multi(system, p12, f12, ss.solve_opts(iters, 1.0, block_threads=bt), info,
-                                       rhs_per_cta=rc)
-                        ev1.record()
-                        torch.cuda.synchronize()
-                        ts.append(ev0.elapsed_time(ev1))
-                except ss.SplitSartError:
-                    continue
-                t = min(ts[1:])
-                if t < best_t:
-                    best, best_t = {"rhs_per_cta": rc, "block_threads": bt}, t
+            for bt in (128, 256, 512, 640, 768, 1024):
+                for lpr in (2, 4, 8):
+                    if rc * lpr > 32:
+                        continue
+                    try:
+                        ts = []
+                        for r in range(3):
+                            f12.copy_(f0)
+                            ev0.record()
+                            ss.solve_multi(system, p12, f12,
+                                           ss.solve_opts(iters, 1.0, block_threads=bt, lanes_per_row=lpr), info,
+                                           rhs_per_cta=rc)
+                            ev1.record()
+                            torch.cuda.synchronize()
+                            ts.append(ev0.elapsed_time(ev1))
+                    except ss.SplitSartError:
+                        continue
+                    t = min(ts[1:])
+                    if t < best_t:
+                        best, best_t = {"rhs_per_cta": rc, "block_threads": bt, "lanes_per_row": lpr}, t
         f12.copy_(f0)
         if best is None:
-            best = {"rhs_per_cta": 0, "block_threads": 0}
+            best = {"rhs_per_cta": 0, "block_threads": 0, "lanes_per_row": 0}
         if use_cache:
             cache[key] = best
             _store(cache)

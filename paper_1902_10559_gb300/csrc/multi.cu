@@ -286,12 +286,9 @@ size_t multi_smem_bytes(const splitsart_system* s, int S, int RC) {
            2 * al(vb * s->Nh * RC);
 }
 
-template <class T, int RC>
+template <class T, int RC, int RPW>
 int launch_multi(splitsart_system* s, int S, int nrhs, const void* p12, void* f12, const splitsart_solve_opts& o,
                  const int32_t* order, splitsart_solve_info* info, cudaStream_t st) {
-    // Four lane groups per warp: up to 8 lanes per (row, right-hand side), about one
-    // entry each for a slice whose rows hold tens of entries.
-    constexpr int RPW = RC >= 4 ? 1 : 4 / RC;
     auto kern = sart_multi_kernel<T, RC, RPW>;
     const size_t dyn = multi_smem_bytes<T>(s, S, RC);
     int dev = 0, optin = 0;
@@ -350,15 +347,31 @@ int launch_multi(splitsart_system* s, int S, int nrhs, const void* p12, void* f1
     return e == cudaSuccess ? SPLITSART_OK : cuda_fail(e, "solve_multi: launch");
 }
 
+// Lanes per (row, right-hand side): LPR = 32 / (RC RPW). With 2 lanes (the
+// default) a warp of one right-hand side per CTA sums 16 rows at once, and the
+// tiny slice's 320 rows and 256 columns take one sweep each of a 512-thread
+// CTA. On 64 right-hand sides of the tiny slice (one per CTA, 200 iterations)
+// 2 lanes ran 0.765 ms at 512 threads, against 0.964 ms for 8 lanes at 1024
+// threads (the earlier fixed shape), 0.815 ms for 4 lanes and 0.790 ms for 1.
+template <class T, int RC>
+int multi_lpr(splitsart_system* s, int S, int nrhs, const void* p12, void* f12, const splitsart_solve_opts& o,
+              const int32_t* order, splitsart_solve_info* info, cudaStream_t st) {
+    const int lpr = o.lanes_per_row > 0 ? o.lanes_per_row : 2;
+    if (lpr == 2 && RC <= 16) return launch_multi<T, RC, (RC <= 16 ? 16 / RC : 1)>(s, S, nrhs, p12, f12, o, order, info, st);
+    if (lpr == 4 && RC <= 8) return launch_multi<T, RC, (RC <= 8 ? 8 / RC : 1)>(s, S, nrhs, p12, f12, o, order, info, st);
+    if (lpr == 8 && RC <= 4) return launch_multi<T, RC, (RC <= 4 ? 4 / RC : 1)>(s, S, nrhs, p12, f12, o, order, info, st);
+    return fail(SPLITSART_ERR_ARG, "solve_multi: lanes_per_row must be 2, 4 or 8, with rhs_per_cta x lanes_per_row <= 32");
+}
+
 template <class T>
 int multi_typed(splitsart_system* s, int S, int nrhs, int rc, const void* p12, void* f12,
                 const splitsart_solve_opts& o, const int32_t* order, splitsart_solve_info* info, cudaStream_t st) {
     switch (rc) {
-        case 1: return launch_multi<T, 1>(s, S, nrhs, p12, f12, o, order, info, st);
-        case 2: return launch_multi<T, 2>(s, S, nrhs, p12, f12, o, order, info, st);
-        case 4: return launch_multi<T, 4>(s, S, nrhs, p12, f12, o, order, info, st);
-        case 8: return launch_multi<T, 8>(s, S, nrhs, p12, f12, o, order, info, st);
-        case 16: return launch_multi<T, 16>(s, S, nrhs, p12, f12, o, order, info, st);
+        case 1: return multi_lpr<T, 1>(s, S, nrhs, p12, f12, o, order, info, st);
+        case 2: return multi_lpr<T, 2>(s, S, nrhs, p12, f12, o, order, info, st);
+        case 4: return multi_lpr<T, 4>(s, S, nrhs, p12, f12, o, order, info, st);
+        case 8: return multi_lpr<T, 8>(s, S, nrhs, p12, f12, o, order, info, st);
+        case 16: return multi_lpr<T, 16>(s, S, nrhs, p12, f12, o, order, info, st);
     }
     return fail(SPLITSART_ERR_ARG, "solve_multi: rhs_per_cta must be 1, 2, 4, 8 or 16");
 }

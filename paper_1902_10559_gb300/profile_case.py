@@ -30,6 +30,7 @@ def main():
     ap.add_argument("--lpc", type=int, default=4)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0, help="kernels 7 and 8: chunk entry target (0 = library default)")
+    ap.add_argument("--lpr", type=int, default=0, help="lanes per row (kernels 7 and 8; multi); 0 = library default")
     ap.add_argument("--nrhs", type=int, default=64)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--rc", type=int, default=0, help="multi: right-hand sides per CTA (0 = library choice)")
@@ -56,6 +57,7 @@ def main():
         ss.fold_rhs(sysm, p, p12)
         f12 = torch.zeros(sysm.Nh, 2, device=dev)
         opts = ss.solve_opts(args.iters, 0.8, kernel=args.kernel, lanes_per_col=args.lpc, tile_entries=args.tile,
+                             lanes_per_row=args.lpr,
                              block_threads=args.threads)
         for _ in range(2):
             f12.zero_()
@@ -73,8 +75,8 @@ def main():
         info = torch.zeros(args.nrhs * ctypes.sizeof(ss.SolveInfo), dtype=torch.uint8, device=dev)
         for _ in range(2):
             f12.zero_()
-            ss.solve_multi(sysm, p12, f12, ss.solve_opts(args.iters, 0.8, block_threads=args.threads), info,
-                           rhs_per_cta=args.rc)
+            ss.solve_multi(sysm, p12, f12, ss.solve_opts(args.iters, 0.8, block_threads=args.threads,
+                                                          lanes_per_row=args.lpr), info, rhs_per_cta=args.rc)
         torch.cuda.synchronize()
         print("multi", ss.read_infos(info, 1)[0])
     else:

@@ -39,7 +39,7 @@ def case():
     return g, A1, A2, ps
 
 
-def run(ss, system, ps, iters, lam, tol=0.0, rc=0):
+def run(ss, system, ps, iters, lam, tol=0.0, rc=0, lpr=0):
     vt = system.vec_dtype
     n = len(ps)
     p = torch.as_tensor(np.stack(ps), dtype=vt, device="cuda")
@@ -48,13 +48,15 @@ def run(ss, system, ps, iters, lam, tol=0.0, rc=0):
         ss.fold_rhs(system, p[r].contiguous(), p12[r])
     f12 = torch.zeros(n, system.Nh, 2, dtype=vt, device="cuda")
     info = torch.zeros(n * ctypes.sizeof(ss.SolveInfo), dtype=torch.uint8, device="cuda")
-    ss.solve_multi(system, p12, f12, ss.solve_opts(iters, lam, tol), info, rhs_per_cta=rc)
+    ss.solve_multi(system, p12, f12, ss.solve_opts(iters, lam, tol, lanes_per_row=lpr), info, rhs_per_cta=rc)
     torch.cuda.synchronize()
     return ss.read_infos(info, n), f12.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("dt,tol,rc", [("f64", 1e-10, 4), ("f32", 1e-4, 1), ("f32", 1e-4, 8), ("bf16", 1e-4, 16)])
-def test_multi_rhs_matches_oracle(ss, case, dt, tol, rc):
+@pytest.mark.parametrize("dt,tol,rc,lpr", [("f64", 1e-10, 4, 0), ("f64", 1e-10, 1, 8), ("f32", 1e-4, 1, 0),
+                                           ("f32", 1e-4, 1, 4), ("f32", 1e-4, 8, 4), ("f32", 1e-4, 2, 8),
+                                           ("bf16", 1e-4, 16, 0)])
+def test_multi_rhs_matches_oracle(ss, case, dt, tol, rc, lpr):
     """Each right-hand side against the oracle, element by element.
 
     For BF16 values the oracle runs on the stored (dequantised) matrix, which
@@ -69,17 +71,25 @@ def test_multi_rhs_matches_oracle(ss, case, dt, tol, rc):
         shape = (g.M // 2, g.N // 2)
         B1 = sp.csr_matrix((out["a1"], out["col"], out["row_ptr"]), shape=shape)
         B2 = sp.csr_matrix((out["a2"], out["col"], out["row_ptr"]), shape=shape)
-    infos, f12 = run(ss, system, ps, 100, 1.0, rc=rc)
+    infos, f12 = run(ss, system, ps, 100, 1.0, rc=rc, lpr=lpr)
     for r in (0, 1, 17, 63):
         p1, p2 = osplit.fold_rhs(ps[r])
         ref = osart.split_sart(B1, B2, p1, p2, 1.0, 100)
         f_ref = osplit.recombine(ref["f1"], ref["f2"])
         f = osplit.recombine(f12[r, :, 0], f12[r, :, 1])
         assert infos[r]["iters"] == 100 and infos[r]["status"] == 0
-        close(f, f_ref, tol, f"right-hand side {r} ({dt}, {rc} per CTA)")
+        close(f, f_ref, tol, f"right-hand side {r} ({dt}, {rc} per CTA, {lpr or 2} lanes per row)")
         if dt == "bf16":
             exact = osart.split_sart(A1, A2, p1, p2, 1.0, 100)
             close_norm(f, osplit.recombine(exact["f1"], exact["f2"]), 2e-3, f"right-hand side {r}: BF16 storage")
+
+
+def test_multi_rhs_rejects_too_many_lanes(ss, case):
+    g, A1, A2, ps = case
+    system = ss.fold_system(ss.make_geometry(g), ss.F32)
+    with pytest.raises(ss.SplitSartError) as e:
+        run(ss, system, ps[:4], 5, 1.0, rc=8, lpr=8)  # 8 x 8 lanes exceed a warp
+    assert e.value.code == ss.ERR_ARG
 
 
 def test_multi_rhs_stop_individually(ss, case):
