@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(1024, 1) sart_multi_kernel(MultiArgs<T> a) {
     constexpr int LPR = 32 / (RC * RPW);  // lanes per (row, right-hand side)
     static_assert(LPR >= 1, "too many groups per warp");
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double s_rr[32][RPW][RC];  // per warp (at most 32) and lane group
+    __shared__ double s_rr[32][RC];  // per warp (at most 32) and slot: ||r||^2 of the warp's rows
     __shared__ double s_pp[RC];
     __shared__ int s_rhs[RC];    // right-hand side held by each slot, or -1
     __shared__ int s_k[RC];      // iterations done by the slot's right-hand side
@@ -195,21 +195,30 @@ __global__ void __launch_bounds__(1024, 1) sart_multi_kernel(MultiArgs<T> a) {
                 rr.add(r1, r2);
             }
         }
-        if (sub == 0) s_rr[wib][rw][g] = rr.sum();
+        {
+            // The warp's sum per slot: a fixed xor tree over its RPW lane groups of the slot
+            // (lanes with sub != 0 hold 0 and pair only with each other).
+            double t = rr.sum();
+#pragma unroll
+            for (int o = RC * LPR; o < 32; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane < RC * LPR && sub == 0) s_rr[wib][g] = t;
+        }
         if (tid == 0) s_fin = 0u;
         __syncthreads();
         // ---- stop tests, overlapped with the back-projection ----
-        // One warp per slot sums its partials (lane-strided, fixed tree; FP64 is
-        // slow on this GPU, so no serial chain) and its lane 0 decides. The other
-        // warps start the back-projection meanwhile: it writes f^{k+1} into the
-        // second buffer, so a slot that stops still holds f^k in the first.
-        for (int r = wib; r < RC; r += nwarps) {
+        // One warp per slot sums the warps' partials (lane-strided, fixed tree; FP64
+        // is slow on this GPU, so no serial chain) and its lane 0 decides. The last
+        // warps take the tests: when the columns do not fill every warp, they have
+        // no back-projection work. The other warps back-project meanwhile: that
+        // writes f^{k+1} into the second buffer, so a slot that stops still holds
+        // f^k in the first.
+        for (int r = nwarps - 1 - wib; r < RC; r += nwarps) {
             if (s_rhs[r] < 0) continue;  // uniform over the warp
             const int k = s_k[r];
             const bool last = k >= a.max_iters;
             if (!(last || (k % a.check_every == 0))) continue;
             double t0 = 0.0;
-            for (int x = lane; x < nwarps * RPW; x += 32) t0 += s_rr[x / RPW][x % RPW][r];
+            for (int x = lane; x < nwarps; x += 32) t0 += s_rr[x][r];
             t0 = warp_sum(t0);
             if (lane == 0) {
                 const double t1 = s_pp[r];
