@@ -627,7 +627,7 @@ void splitsart_cnn_destroy(splitsart_cnn* cnn);
 /* Arithmetic of the two 32 -> 32 layers:
  * - 0: FP32 on the CUDA cores (default);
  * - 1: BF16 tcgen05 tensor-core MMAs with FP32 accumulation in tensor
- *   memory (needs nx = 32 and nz*nx a multiple of 128).
+ *   memory, on tiles of 128 consecutive pixels of the batch (any nz, nx).
  * Layers 1 and 4, the weight gradients and Adam are FP32 in both modes. */
 int splitsart_cnn_set_mode(splitsart_cnn* cnn, int mode);
 

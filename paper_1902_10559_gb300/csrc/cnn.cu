@@ -391,7 +391,7 @@ extern "C" void splitsart_cnn_destroy(splitsart_cnn* n) {
 
 extern "C" int splitsart_cnn_set_mode(splitsart_cnn* n, int mode) {
     if (!n || mode < 0 || mode > 1) return fail(SPLITSART_ERR_ARG, "cnn_set_mode: mode must be 0 or 1");
-    if (mode == 1 && !cnn_mma_supported(n)) return fail(SPLITSART_ERR_ARG, "cnn_set_mode: tensor-core mode needs nx*nz divisible by 128 and nx == 32");
+    if (mode == 1 && !cnn_mma_supported(n)) return fail(SPLITSART_ERR_ARG, "cnn_set_mode: tensor-core mode needs a non-empty image");
     n->mode = mode;
     return SPLITSART_OK;
 }

@@ -6,7 +6,8 @@
 //            B[co][k] = W[co][ci][tap]
 //   input gradient: the same GEMM with the taps flipped (p - tap + 1) and
 //            B[ci][k = tap*32 + co] = W[co][ci][tap].
-// One CTA computes a 128-pixel tile (four image rows of 32 pixels) for all 32
+// One CTA computes a tile of 128 consecutive pixels of the batch (in
+// [image][y][x] order, any image size; the last tile is padded) for all 32
 // channels: M = 128, N = 32, K = 288.
 //
 // sm_100-family tensor cores (tcgen05), BF16 x BF16 -> FP32:
@@ -83,8 +84,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, unsign
 template <bool BWD>
 __global__ void __launch_bounds__(256) conv32_mma_kernel(const float* __restrict__ in, const float* __restrict__ Wt,
                                                          const float* __restrict__ bias, const float* __restrict__ act,
-                                                         float* __restrict__ out, int H, int* __restrict__ err) {
-    constexpr int Wd = 32;
+                                                         float* __restrict__ out, int B, int H, int Wd,
+                                                         int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;
     unsigned char* sB = smem + kA_bytes;
@@ -93,8 +94,8 @@ __global__ void __launch_bounds__(256) conv32_mma_kernel(const float* __restrict
     __shared__ int s_ok;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tiles_per_img = H / 4;
-    const int b = blockIdx.x / tiles_per_img, y0 = (blockIdx.x % tiles_per_img) * 4;
+    const long long HW = (long long)H * Wd, total = (long long)B * HW;
+    const long long P0 = (long long)blockIdx.x * kM;  // the tile's first pixel
 
     // TMEM: 32 columns (the minimum allocation), by warp 0.
     if (warp == 0) {
@@ -109,16 +110,19 @@ __global__ void __launch_bounds__(256) conv32_mma_kernel(const float* __restrict
         s_ok = 1;
     }
 
-    // A: 128 pixels x 36 chunks of 8 channels (one tap each), converted to BF16.
+    // A: 128 pixels x 36 chunks of 8 channels (one tap each), converted to BF16;
+    // zero rows past the batch's last pixel.
     for (int c = tid; c < kM * (kK / 8); c += blockDim.x) {
         const int m = c / (kK / 8), kc = c % (kK / 8);
         const int tap = kc / 4, ci0 = (kc % 4) * 8;
         const int dy = tap / 3, dx = tap % 3;
-        const int py = y0 + m / Wd, px = m % Wd;
+        const long long P = P0 + m;
+        const int b = (int)(P / HW), rem = (int)(P - (long long)b * HW);
+        const int py = rem / Wd, px = rem - py * Wd;
         const int iy = BWD ? py + 1 - dy : py + dy - 1;
         const int ix = BWD ? px + 1 - dx : px + dx - 1;
         uint4 pack = make_uint4(0, 0, 0, 0);
-        if (iy >= 0 && iy < H && ix >= 0 && ix < Wd) {
+        if (P < total && iy >= 0 && iy < H && ix >= 0 && ix < Wd) {
             const float4* src = reinterpret_cast<const float4*>(in + (((size_t)b * H + iy) * Wd + ix) * 32 + ci0);
             const float4 v0 = src[0], v1 = src[1];
             __nv_bfloat162 h0 = __floats2bfloat162_rn(v0.x, v0.y), h1 = __floats2bfloat162_rn(v0.z, v0.w);
@@ -185,10 +189,10 @@ __global__ void __launch_bounds__(256) conv32_mma_kernel(const float* __restrict
                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const int m = warp * 32 + lane;
-            const size_t base = (((size_t)b * H + y0 + m / Wd) * Wd + m % Wd) * 32;
+            const long long P = P0 + warp * 32 + lane;  // this thread's pixel; [image][y][x] is P itself
+            const size_t base = (size_t)P * 32;
 #pragma unroll
-            for (int c = 0; c < 32; c += 4) {
+            for (int c = 0; c < 32 && P < total; c += 4) {
                 float4 o;
                 float* po = &o.x;
 #pragma unroll
@@ -218,7 +222,9 @@ int launch_mma(splitsart_cnn* n, const float* in, const float* W, const float* b
     const size_t smem = kA_bytes + kB_bytes;
     cudaError_t e = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cnn mma: shared memory attribute");
-    k<<<B * (n->H / 4), 256, smem, st>>>(in, W, b, act, out, n->H, reinterpret_cast<int*>(n->mma_scratch));
+    const long long pixels = (long long)B * n->H * n->W;
+    const unsigned tiles = (unsigned)((pixels + kM - 1) / kM);
+    k<<<tiles, 256, smem, st>>>(in, W, b, act, out, B, n->H, n->W, reinterpret_cast<int*>(n->mma_scratch));
     e = cudaGetLastError();
     return e == cudaSuccess ? SPLITSART_OK : cuda_fail(e, "cnn mma: launch");
 }
@@ -227,7 +233,7 @@ int launch_mma(splitsart_cnn* n, const float* in, const float* W, const float* b
 
 size_t cnn_mma_scratch_bytes(int, int, int) { return 256; }  // one error word
 
-bool cnn_mma_supported(const splitsart_cnn* n) { return n->W == 32 && n->H % 4 == 0; }
+bool cnn_mma_supported(const splitsart_cnn* n) { return n->W > 0 && n->H > 0; }
 
 int cnn_mma_conv_fwd(splitsart_cnn* n, const float* in, const float* W, const float* b, float* out, int B,
                      cudaStream_t st) {
