@@ -294,8 +294,9 @@ class Realistic:
         per_us = solve_ms * 1e3 / self.iters
         return {"bound": "latency", "floor_us_per_iteration": floor_us, "us_per_iteration": per_us,
                 "frac": floor_us / per_us,
-                "floor_from": "the same kernel and launch shape on the tiny slice (3,394 entries): two grid barriers, "
-                              "the norm reduction, the stop test and one round of dependent gathers each way"}
+                "floor_from": "the same kernel and launch shape on the tiny slice (3,394 entries): two grid barriers "
+                              "and one round of dependent gathers each way per iteration (with tol = 0, as here, "
+                              "rho is tested at the first and the last iteration only)"}
 
     def extra(self, ss):
         """Workload-specific keys added to the JSON line."""

@@ -288,8 +288,9 @@ int splitsart_project(splitsart_system* sys, const void* f_dev, int layout, void
 typedef struct splitsart_solve_opts {
     int32_t max_iters;     /* iteration cap, in [0, 500000] */
     double lambda;         /* relaxation, 0 < lambda < 2 */
-    double tol;            /* stop at the first k with rho_k <= tol; 0 = run max_iters */
-    int32_t check_every;   /* test rho every this many iterations (>= 1; 0 means 1) */
+    double tol;            /* stop at the first k with rho_k <= tol; 0 = run max_iters (rho is then tested only
+                              at k = 0, where p = 0 stops at once, and at k = max_iters) */
+    int32_t check_every;   /* test rho every this many iterations (>= 1; 0 means 1); not used when tol = 0 */
     int32_t block_threads; /* threads per CTA, multiple of 32 in [64, 1024]; 0 = the kernel's default.
                               Kernel 1: default 1024. Kernels 2 and 3: at most 512 (default 512;
                               larger values run 512). Kernel 4: at most 384 (default 384) */

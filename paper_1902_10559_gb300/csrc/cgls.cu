@@ -384,7 +384,7 @@ int launch_cgls(splitsart_system* s, const void* p12, void* f12, const splitsart
     a.Mh = (int)s->Mh;
     a.Nh = (int)s->Nh;
     a.max_iters = o.max_iters;
-    a.check_every = o.check_every > 0 ? o.check_every : 1;
+    a.check_every = effective_check_every(o);
     a.tol = o.tol;
     a.tol2_hi = o.tol * o.tol * (1.0 + 1e-12);
     const double tms = o.timeout_ms > 0 ? o.timeout_ms : 2000.0;

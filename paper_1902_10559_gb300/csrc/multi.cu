@@ -163,7 +163,16 @@ __global__ void __launch_bounds__(1024, 1) sart_multi_kernel(MultiArgs<T> a) {
     load_slots((1u << RC) - 1u, s_f);
     __syncthreads();
 
+    // Every thread's copy of s_k, kept in step at points where s_rhs is not being written.
+    int kl[RC];
+#pragma unroll
+    for (int r = 0; r < RC; ++r) kl[r] = 0;
     for (;;) {
+        // Whether any slot tests rho after this pass (uniform over the CTA): the
+        // residual norms are formed only then.
+        bool tested = false;
+#pragma unroll
+        for (int r = 0; r < RC; ++r) tested |= s_rhs[r] >= 0 && (kl[r] >= a.max_iters || kl[r] % a.check_every == 0);
         // ---- forward: RPW rows per warp, one lane group per (row, slot) ----
         SqAcc<Acc> rr;  // this lane group's ||r||^2 over its rows
         for (int i0 = wib * RPW; i0 < Mh; i0 += nwarps * RPW) {
@@ -192,10 +201,10 @@ __global__ void __launch_bounds__(1024, 1) sart_multi_kernel(MultiArgs<T> a) {
                 const Acc r1 = p.x - s1, r2 = p.y - s2;
                 // For BF16/FP16, ir already holds the row scale (the codes are reused by the back-projection).
                 s_u[i * RC + g] = V2{r1 * ir.x, r2 * ir.y};
-                rr.add(r1, r2);
+                if (tested) rr.add(r1, r2);
             }
         }
-        {
+        if (tested) {
             // The warp's sum per slot: a fixed xor tree over its RPW lane groups of the slot
             // (lanes with sub != 0 hold 0 and pair only with each other).
             double t = rr.sum();
@@ -257,6 +266,8 @@ __global__ void __launch_bounds__(1024, 1) sart_multi_kernel(MultiArgs<T> a) {
         __syncthreads();
         const unsigned fin = s_fin;  // read by every thread before any later write of s_fin
         if (tid < RC && s_rhs[tid] >= 0) ++s_k[tid];
+#pragma unroll
+        for (int r = 0; r < RC; ++r) kl[r] += s_rhs[r] >= 0 ? 1 : 0;
         if (fin) {
             // Return the stopped right-hand sides' f^k and refill their slots from
             // the queue; a new right-hand side's f0 goes into the buffer that the
@@ -276,6 +287,9 @@ __global__ void __launch_bounds__(1024, 1) sart_multi_kernel(MultiArgs<T> a) {
                 s_active = active;
             }
             __syncthreads();
+#pragma unroll
+            for (int r = 0; r < RC; ++r)
+                if (fin >> r & 1u) kl[r] = 0;
             if (s_active == 0) break;
             load_slots(fin, s_fn);
             __syncthreads();
@@ -331,7 +345,7 @@ int launch_multi(splitsart_system* s, int S, int nrhs, const void* p12, void* f1
     a.S = S;
     a.nrhs = nrhs;
     a.max_iters = o.max_iters;
-    a.check_every = o.check_every > 0 ? o.check_every : 1;
+    a.check_every = effective_check_every(o);
     a.lambda = o.lambda;
     a.tol = o.tol;
     a.tol2_hi = o.tol * o.tol * (1.0 + 1e-12);

@@ -420,7 +420,7 @@ int launch_os(splitsart_system* s, const void* p12, void* f12, const splitsart_s
     a.Nh = (int)s->Nh;
     a.cone = os.cone ? 1 : 0;
     a.max_iters = o.max_iters;
-    a.check_every = o.check_every > 0 ? o.check_every : 1;
+    a.check_every = effective_check_every(o);
     a.lambda = o.lambda;
     a.tol = o.tol;
     a.tol2_hi = o.tol * o.tol * (1.0 + 1e-12);

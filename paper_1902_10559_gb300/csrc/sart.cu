@@ -1622,7 +1622,7 @@ void fill_args(SartArgs<T>& a, splitsart_system* s, const void* p12, void* f12, 
     a.result = s->result;
     a.stats = s->stats;
     a.max_iters = o.max_iters;
-    a.check_every = o.check_every > 0 ? o.check_every : 1;
+    a.check_every = effective_check_every(o);
     a.lambda = o.lambda;
     a.tol = o.tol;
     a.tol2_hi = o.tol * o.tol * (1.0 + 1e-12);
@@ -1993,7 +1993,7 @@ int launch_static(StaticScratch* sc, int Mh, int Nh, const int32_t* rp, const in
     a.ctl = &sc->ctl;
     a.result = &sc->result;
     a.max_iters = o.max_iters;
-    a.check_every = o.check_every > 0 ? o.check_every : 1;
+    a.check_every = effective_check_every(o);
     a.lambda = o.lambda;
     a.tol = o.tol;
     a.tol2_hi = o.tol * o.tol * (1.0 + 1e-12);

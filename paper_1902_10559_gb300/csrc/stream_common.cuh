@@ -323,7 +323,7 @@ inline StArgs<T, kImplicit> st_args(splitsart_system* s, const StreamFmt& F, con
     a.sl_solve = s->sl_solve;
     a.ndone = s->ndone;
     a.max_iters = o.max_iters;
-    a.check_every = o.check_every > 0 ? o.check_every : 1;
+    a.check_every = effective_check_every(o);
     a.lambda = o.lambda;
     a.tol = o.tol;
     a.tol2_hi = o.tol * o.tol * (1.0 + 1e-12);

@@ -197,6 +197,14 @@ struct splitsart_system {
 };
 
 namespace splitsart {
+// The iterations at which a solve tests rho: every check_every-th (0 means 1).
+// With tol = 0 only an exactly zero residual could stop the solve before
+// max_iters, and from then on f no longer changes, so rho is tested only at
+// k = 0 (where p = 0 still stops at once) and at k = max_iters.
+inline int effective_check_every(const splitsart_solve_opts& o) {
+    if (o.tol == 0.0 && o.max_iters > 0) return o.max_iters;
+    return o.check_every > 0 ? o.check_every : 1;
+}
 inline SliceMap slice_map(const splitsart_system* s) {
     return SliceMap{s->ns, s->sl_rows, s->sl_cols, s->sl_M, s->sl_N, s->sl_nx, s->sl_nz};
 }
