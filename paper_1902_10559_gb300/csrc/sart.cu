@@ -813,17 +813,19 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
                     if (q + k * nwarps < nr) fin_row(q + k * nwarps, s1[k], s2[k]);
             }
         }
-        if (lane == 0) s_rrw[wib] = rr.sum();
-        __syncthreads();
-        if (wib == 0) {
-            const double t = warp_sum(lane < nwarps ? s_rrw[lane] : 0.0);
-            if (lane == 0) __stcg(a.partials + 2 * blockIdx.x, t + ppz);  // an empty row's residual is its p
+        const bool last = (k >= a.max_iters);
+        const bool check = last || (k % a.check_every == 0);
+        if (check) {  // the CTA's ||r||^2, only where the stop test reads it (uniform over the grid)
+            if (lane == 0) s_rrw[wib] = rr.sum();
+            __syncthreads();
+            if (wib == 0) {
+                const double t = warp_sum(lane < nwarps ? s_rrw[lane] : 0.0);
+                if (lane == 0) __stcg(a.partials + 2 * blockIdx.x, t + ppz);  // an empty row's residual is its p
+            }
         }
         if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
 
         // ---- back-projection; the stop test reads its totals while the first gathers fly ----
-        const bool last = (k >= a.max_iters);
-        const bool check = last || (k % a.check_every == 0);
         auto fin_col = [&](int q, Acc b1, Acc b2) {
             const N2 ic = c_ic[q];
             V2 f = c_f[q];
