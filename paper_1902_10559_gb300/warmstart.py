@@ -50,7 +50,8 @@ class WarmStart:
         self.geom = ss.make_geometry(g)
         self.system = ss.fold_system(self.geom, ss.F32)
         self.chunk = chunk
-        self.vec = ss.fold_batch([self.geom] * chunk, ss.F32)  # [chunk][...] layouts for the vector folds
+        # [n][...] layouts for the vector folds: a batch of n copies of the slice, made once per n.
+        self._vecs = {chunk: ss.fold_batch([self.geom] * chunk, ss.F32)}
         self.cnn = ss.Cnn(g.nz, g.nx, max_batch, cnn_initial_params() if params is None else params)
         self.steps = 0  # Adam steps taken
         if mode:
@@ -63,7 +64,9 @@ class WarmStart:
             yield a, min(a + self.chunk, n)
 
     def _vec_for(self, n):
-        return self.vec if n == self.chunk else ss.fold_batch([self.geom] * n, ss.F32)
+        if n not in self._vecs:
+            self._vecs[n] = ss.fold_batch([self.geom] * n, ss.F32)
+        return self._vecs[n]
 
     def project(self, images):
         """images: CUDA float32 [n][nz][nx] -> p [n][M]."""
