@@ -18,14 +18,15 @@
 //   ring, so no space is set aside for the longest row; the producer waits
 //   for the oldest chunks to be released before it writes over their bytes.
 //   A sentinel chunk without bytes ends each pass.
-// - Consumers. Fifteen warps take the rows of each chunk in groups of R,
-//   dealt round robin across chunks, read the entries from shared memory and
-//   spend their waits on the gathers of f (of u in the back pass) alone. Each
-//   warp releases a chunk on its slot's second mbarrier when it is done with
-//   its groups.
-// The per-row and per-column sums keep the lane-strided order and shuffle tree
-// of kernels 5 and 6, so at equal lanes_per_col kernel 7 returns kernel 5's f
-// and kernel 8 kernel 6's, bit for bit.
+// - Consumers. The other warps (23, or 15 for FP64 vectors) take the rows of
+//   each chunk in groups, dealt round robin across chunks, read the entries
+//   from shared memory and spend their waits on the gathers of f (of u in the
+//   back pass) alone. Each warp releases a chunk on its slot's second mbarrier
+//   when it is done with its groups.
+// With the whole warp on a row (lanes_per_row 32, the default) the per-row and
+// per-column sums keep the lane-strided order and shuffle tree of kernels 5
+// and 6, so at equal lanes_per_col kernel 7 returns kernel 5's f and kernel 8
+// kernel 6's, bit for bit.
 #include <algorithm>
 #include <cstdio>
 
@@ -34,7 +35,7 @@
 namespace splitsart {
 namespace {
 
-constexpr int kRingSlots = 32;                           // chunks outstanding per CTA at most
+constexpr int kRingSlots = 32;  // chunks outstanding per CTA at most
 
 // Header of a chunk in the ring, written by the producer before its arrival on
 // the slot's full barrier.
@@ -83,7 +84,6 @@ __global__ void ring_plan_kernel(const int32_t* __restrict__ ptr, const int* __r
         desc[c] = make_int2(q, ptr[q]);
     }
 }
-
 
 template <class T, bool kImplicit>
 struct RingArgs {
