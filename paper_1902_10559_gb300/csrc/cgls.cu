@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(512, 1) cgls_kernel(CgArgs<T> a) {
         const int sl[2] = {0, 5};
         cta_publish(v, sl, a.part, s_red);
     }
-    if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+    if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     // ---- prologue 2: s^0 = A^T r^0, d^{-1} = 0, gamma_0 ----
     {
         double g1 = 0.0, g2 = 0.0;
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(512, 1) cgls_kernel(CgArgs<T> a) {
         const int sl[2] = {3, 4};
         cta_publish(v, sl, a.part, s_red);
     }
-    if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+    if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     if (wib == 0) {
         const double pp = slot_total(a.part, 5, lane);
         const double g1 = slot_total(a.part, 3, lane);
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(512, 1) cgls_kernel(CgArgs<T> a) {
             const int sl[3] = {0, 1, 2};
             cta_publish(v, sl, a.part, s_red);
         }
-        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+        if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
         // ---- stop test on ||r^k||, then alpha_k (one thread; every CTA alike) ----
         const bool last = k >= a.max_iters;
         if (wib == 0) {
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(512, 1) cgls_kernel(CgArgs<T> a) {
             const int sl[2] = {3, 4};
             cta_publish(v, sl, a.part, s_red);
         }
-        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+        if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
         // ---- beta_k and gamma_{k+1} ----
         if (wib == 0) {
             const double g1 = slot_total(a.part, 3, lane);

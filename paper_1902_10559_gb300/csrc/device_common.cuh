@@ -146,17 +146,29 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
 
 // Control block of one persistent launch. The host zeroes it before each launch.
 struct LaunchCtl {
-    unsigned bar_count;
-    unsigned bar_gen;
-    int err;          // 0, or a SPLITSART_ERR_* code
-    int err_where;    // barrier index at which a wait ran out
-    unsigned work[2]; // work counters of dynamically scheduled passes (forward, back)
+    unsigned long long bar_count;  // barrier arrivals; bit 63 set once an error is recorded
+    int err;                       // 0, or a SPLITSART_ERR_* code
+    int err_where;                 // barrier index at which a wait ran out
+    unsigned work[2];              // work counters of dynamically scheduled passes (forward, back)
 };
+constexpr unsigned long long kBarError = 1ull << 63;
+
+// Record a launch error (the first one recorded wins) and raise the error bit
+// of the barrier count, so that every CTA leaves at its next grid barrier.
+__device__ __forceinline__ void record_error(LaunchCtl* ctl, int code, int where) {
+    if (atomicCAS(&ctl->err, 0, code) == 0) ctl->err_where = where;
+    atomicOr(&ctl->bar_count, kBarError);
+}
 
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).
 // ctl->bar_count only ever grows during a launch:
@@ -164,41 +176,41 @@ struct LaunchCtl {
 //   needs no round trip; no separate fence);
 // - it then waits until the count reaches `target`, which is
 //   expected x (barrier index + 1).
-// The wait has a wall-clock limit (checked every 64 polls) and a spin cap. If
-// either runs out, the wait records SPLITSART_ERR_TIMEOUT in ctl->err and
-// stops waiting. `expected` is normally gridDim.x; a test passes gridDim.x + 1
-// to make the wait run out on purpose.
+// An error recorded by any CTA sets bit 63 of the same word, so one acquire
+// load per poll sees both the arrivals and the error. The wait has a
+// wall-clock limit (checked every 64 polls) and a spin cap. If either runs
+// out, the wait records SPLITSART_ERR_TIMEOUT and stops waiting. `expected`
+// is normally gridDim.x; a test passes gridDim.x + 1 to make the wait run out
+// on purpose.
 // Returns false, for every thread of the CTA, if this CTA saw an error
 // recorded by any CTA while it waited. The caller must then return. (A CTA
 // that passes a barrier just as another records an error learns of it at the
 // next barrier, which the failed CTA never reaches.)
-__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ bool grid_sync(LaunchCtl* ctl, unsigned target, unsigned long long timeout_ns, int where) {
+__device__ __forceinline__ bool grid_sync(LaunchCtl* ctl, unsigned long long target, unsigned long long timeout_ns,
+                                          int where) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         // The release orders this CTA's earlier writes: the CTA barrier above puts
         // them before this thread's release, and release is cumulative.
-        red_release_add(&ctl->bar_count, 1u);
+        red_release_add(&ctl->bar_count, 1ull);
         const unsigned long long max_spins = timeout_ns / 32ull + (1ull << 20);
         unsigned long long t0 = 0, spins = 0;
         for (;;) {
-            // The error flag is read first, with a plain load, so that it travels with the
-            // acquire load of the count: one round trip per poll.
-            const int err = ld_volatile(&ctl->err);
-            const unsigned count = ld_acquire_gpu(&ctl->bar_count);
-            if (err != 0) {
+            const unsigned long long count = ld_acquire_gpu(&ctl->bar_count);
+            if (count & kBarError) {
                 ok = 0;
                 break;
             }
             if (count >= target) break;
             if (spins == 0) t0 = global_ns();
             if (++spins > max_spins || ((spins & 63) == 0 && global_ns() - t0 > timeout_ns)) {
-                if (atomicCAS(&ctl->err, 0, SPLITSART_ERR_TIMEOUT) == 0) ctl->err_where = where;
+                record_error(ctl, SPLITSART_ERR_TIMEOUT, where);
                 ok = 0;
                 break;
             }

@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(512, 1) os_sart_kernel(OsArgs<T> a) {
             for (int j = blockIdx.x * BD + tid; j < a.Nh; j += gridDim.x * BD) stcg(a.f12 + j, cone_project(ldcg(a.f12 + j)));
     }
     unsigned nbar = 0;
-    if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+    if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     if (wib == 0) {
         const double t = grid_total(a.partials, gridDim.x, lane, 1);
         if (lane == 0) s_tpp = t;
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(512, 1) os_sart_kernel(OsArgs<T> a) {
                 mine += (double)(r1 * r1 + r2 * r2);
             }
             publish_rr(mine);
-            if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+            if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
             if (decide(k, last)) return;
         }
         for (int t = 0; t < a.Tn; ++t) {
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(512, 1) os_sart_kernel(OsArgs<T> a) {
                 }
             }
             if (a.Tn == 1 && check) publish_rr(mine);
-            if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+            if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
             if (a.Tn == 1 && check && decide(k, last)) return;
 
             // ---- back over every non-empty column: f += lambda (A_t^T u) / C_t, then the cone ----
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(512, 1) os_sart_kernel(OsArgs<T> a) {
                     stcg(a.f12 + j, f);
                 }
             }
-            if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+            if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
         }
     }
 }

@@ -129,7 +129,7 @@ __device__ __forceinline__ bool ring_wait(uint64_t* bar, unsigned parity, unsign
 // Record a ring wait that ran out (where: -2 a consumer's wait for a chunk,
 // -3 the producer's wait for a release) and tell the CTA to stop.
 __device__ __forceinline__ void ring_abort(LaunchCtl* ctl, int where, volatile int* abort) {
-    if (atomicCAS(&ctl->err, 0, SPLITSART_ERR_TIMEOUT) == 0) ctl->err_where = where;
+    record_error(ctl, SPLITSART_ERR_TIMEOUT, where);
     *abort = 1;
 }
 
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) sart_ring_kernel(RingArgs<T, 
     const double ppz = st_prologue<T, kImplicit, kBatch>(a, s_red);  // thread 0: empty rows' ||p||^2
     unsigned nbar = 0;
     // The barrier also publishes the mbarrier initialisation to the CTA.
-    if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+    if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     if (!kBatch && wib == 0) {
         const double t = grid_total(a.partials, gridDim.x, lane, 1);
         if (lane == 0) s_tpp = t;
@@ -538,10 +538,10 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) sart_ring_kernel(RingArgs<T, 
             }
             if (pass == 0) {
                 if constexpr (!kBatch) st_rr_partial(rr.sum(), ppz, a.partials, s_red);
-                if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+                if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
                 const int stop = st_stop_test<T, kImplicit, kBatch>(a, k, s_red, s_tpp, &s_stop, nbar);
                 if (stop != 0) return;  // stopped (f written back), or a barrier wait failed
-            } else if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) {
+            } else if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) {
                 return;
             }
         }

@@ -233,13 +233,13 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
         const int nt = plan_tiles(a.nzrp, n_nzr, TE, s_rt, lane);
         if (lane == 0) {
             s_nrt = nt;
-            if (nt < 0) atomicCAS(&a.ctl->err, 0, SPLITSART_ERR_ARG);
+            if (nt < 0) record_error(a.ctl, SPLITSART_ERR_ARG, 0);
         }
     } else if (wib == 1) {
         const int nt = plan_tiles(a.nzcp, n_nzc, TE, s_ct, lane);
         if (lane == 0) {
             s_nct = nt;
-            if (nt < 0) atomicCAS(&a.ctl->err, 0, SPLITSART_ERR_ARG);
+            if (nt < 0) record_error(a.ctl, SPLITSART_ERR_ARG, 0);
         }
     }
     // ||p||^2 is fixed for the launch: this CTA's share of it over all rows
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
         }
         (void)Mh;
     }
-    if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+    if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     const int nrt = s_nrt, nct = s_nct;
     if (!kBatch && wib == 0) {
         const double t = grid_total(a.partials, gridDim.x, lane, 1);
@@ -393,13 +393,13 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
                 if (lane == 0) __stcg(a.partials + 2 * blockIdx.x, t + ppz);  // an empty row's residual is its p
             }
         }
-        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+        if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
 
         const bool last = (k >= a.max_iters);
         if constexpr (kBatch) {
             // ---- per-slice stop tests: one CTA per slice, fixed order ----
             if (last || (k % a.check_every == 0)) slice_stop_tests(a, k, last, s_red[0]);
-            if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+            if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
             if (ld_volatile(a.ndone) >= a.ns) {
                 if (blockIdx.x == 0 && tid == 0) {
                     a.result->iters = k;
@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
             }
             __syncthreads();
         }
-        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+        if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     }
 }
 
@@ -514,9 +514,12 @@ __global__ void __launch_bounds__(1024, 1) sart_stream_kernel(SartArgs<T> a) {
 // Inside a CTA:
 // - forward: one warp per row, NR rows per warp in flight. Lane l takes the
 //   entries l, l + 32, ... of a row; each lane issues up to U gathers per row
-//   before it consumes any, then a shuffle tree sums the row.
+//   before it consumes any, then a shuffle tree sums the row. Every lane ends
+//   with the sums, and lane k finishes row k of the step (r, u and its store),
+//   so the NR rows finish in parallel rather than one after another on lane 0.
 // - back: LPC lanes per column, two groups of columns per warp in flight,
-//   up to UB gathers per lane and column, then a shuffle tree over the group.
+//   up to UB gathers per lane and column, then a shuffle tree over the group;
+//   the group's lanes 0 and 1 finish its two columns.
 // - The stop test of iteration k is decided by one thread per CTA while the
 //   first back-projection gathers are in flight.
 // The sums have a fixed order, so results are deterministic for a given
@@ -696,7 +699,7 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
 
     if (off > (size_t)smem_bytes) {
         // Cannot happen when the host's bound holds; fail cleanly rather than overrun.
-        if (tid == 0) atomicCAS(&a.ctl->err, 0, SPLITSART_ERR_ARG);
+        if (tid == 0) record_error(a.ctl, SPLITSART_ERR_ARG, 0);
         grid_sync(a.ctl, a.expected, a.timeout_ns, 1);
         return;
     }
@@ -765,7 +768,7 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
         }
     }
     unsigned nbar = 0;
-    if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+    if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     if (wib == 0) {
         const double t = grid_total(a.partials, gridDim.x, lane, 1);
         if (lane == 0) s_tot[1] = t;  // read after later CTA barriers
@@ -774,7 +777,7 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
 
     for (int k = 0;; ++k) {
         // ---- forward: r = p - A f, u = r / R, and the norm partials ----
-        SqAcc<Acc> rr;  // lane 0 of each warp: its rows' ||r||^2
+        SqAcc<Acc> rr;  // per lane: the ||r||^2 of the rows it finished
         auto fin_row = [&](int q, Acc s1, Acc s2) {
             const V2 p = r_p[q];
             const N2 ir = r_ir[q];
@@ -807,23 +810,30 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
                 s1[k] = warp_sum(s1[k]);
                 s2[k] = warp_sum(s2[k]);
             }
-            if (lane == 0) {
+            // Every lane holds the sums: lane k finishes row q + k nwarps.
+            if (lane < NR) {
+                Acc t1 = s1[0], t2 = s2[0];
 #pragma unroll
-                for (int k = 0; k < NR; ++k)
-                    if (q + k * nwarps < nr) fin_row(q + k * nwarps, s1[k], s2[k]);
+                for (int k = 1; k < NR; ++k)
+                    if (lane == k) {
+                        t1 = s1[k];
+                        t2 = s2[k];
+                    }
+                if (q + lane * nwarps < nr) fin_row(q + lane * nwarps, t1, t2);
             }
         }
         const bool last = (k >= a.max_iters);
         const bool check = last || (k % a.check_every == 0);
         if (check) {  // the CTA's ||r||^2, only where the stop test reads it (uniform over the grid)
-            if (lane == 0) s_rrw[wib] = rr.sum();
+            const double tw = warp_sum(rr.sum());
+            if (lane == 0) s_rrw[wib] = tw;
             __syncthreads();
             if (wib == 0) {
                 const double t = warp_sum(lane < nwarps ? s_rrw[lane] : 0.0);
                 if (lane == 0) __stcg(a.partials + 2 * blockIdx.x, t + ppz);  // an empty row's residual is its p
             }
         }
-        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+        if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
 
         // ---- back-projection; the stop test reads its totals while the first gathers fly ----
         auto fin_col = [&](int q, Acc b1, Acc b2) {
@@ -863,12 +873,15 @@ __global__ void __launch_bounds__(512, 1) sart_resident_kernel(SartArgs<T> a, in
                 b1[k] = warp_sum(b1[k], LPC);
                 b2[k] = warp_sum(b2[k], LPC);
             }
-            if (sub == 0) {
+            if constexpr (LPC == 1) {
                 if (qA < nc) fin_col(qA, b1[0], b2[0]);
                 if (qB < nc) fin_col(qB, b1[1], b2[1]);
+            } else {  // every lane of the group holds the sums: two lanes finish the two columns
+                if (sub == 0 && qA < nc) fin_col(qA, b1[0], b2[0]);
+                if (sub == 1 && qB < nc) fin_col(qB, b1[1], b2[1]);
             }
         }
-        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+        if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     }
 }
 
@@ -978,7 +991,7 @@ __global__ void __launch_bounds__(512, 1) sart_rows_kernel(SartArgs<T> a) {
         }
     }
     unsigned nbar = 0;
-    if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+    if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     if (!kBatch && wib == 0) {
         const double t = grid_total(a.partials, gridDim.x, lane, 1);
         if (lane == 0) s_tpp = t;  // read after later CTA barriers
@@ -1109,13 +1122,13 @@ __global__ void __launch_bounds__(512, 1) sart_rows_kernel(SartArgs<T> a) {
                 if (lane == 0) __stcg(a.partials + 2 * blockIdx.x, t + ppz);  // an empty row's residual is its p
             }
         }
-        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+        if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
 
         const bool last = (k >= a.max_iters);
         if constexpr (kBatch) {
             // ---- per-slice stop tests: one CTA per slice, fixed order ----
             if (last || (k % a.check_every == 0)) slice_stop_tests(a, k, last, s_red[0]);
-            if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+            if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
             if (ld_volatile(a.ndone) >= a.ns) {
                 if (blockIdx.x == 0 && tid == 0) {
                     a.result->iters = k;
@@ -1188,7 +1201,7 @@ __global__ void __launch_bounds__(512, 1) sart_rows_kernel(SartArgs<T> a) {
                 }
             }
         }
-        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+        if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     }
 }
 
@@ -1294,7 +1307,7 @@ __global__ void __launch_bounds__(384, 1) sart_bulk_kernel(SartArgs<T> a, int te
         }
     }
     unsigned nbar = 0;
-    if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+    if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     if (!kBatch && wib == 0) {
         const double t = grid_total(a.partials, gridDim.x, lane, 1);
         if (lane == 0) s_tpp = t;  // read after later CTA barriers
@@ -1402,7 +1415,7 @@ __global__ void __launch_bounds__(384, 1) sart_bulk_kernel(SartArgs<T> a, int te
             // Job j.
             if (st) {
                 if (!mbar_wait_bounded(&bar[slot], (phase >> slot) & 1u, a.timeout_ns)) {
-                    if (lane == 0 && atomicCAS(&a.ctl->err, 0, SPLITSART_ERR_TIMEOUT) == 0) a.ctl->err_where = -1;
+                    if (lane == 0) record_error(a.ctl, SPLITSART_ERR_TIMEOUT, -1);
                     inflight &= ~(1u << slot);
                     drain();
                     return false;
@@ -1494,12 +1507,12 @@ __global__ void __launch_bounds__(384, 1) sart_bulk_kernel(SartArgs<T> a, int te
             }
         }
         (void)ok_f;  // a failed copy has recorded an error; the barrier below then returns false
-        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+        if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
 
         const bool last = (k >= a.max_iters);
         if constexpr (kBatch) {
             if (last || (k % a.check_every == 0)) slice_stop_tests(a, k, last, s_red[0]);
-            if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+            if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
             if (ld_volatile(a.ndone) >= a.ns) {
                 if (blockIdx.x == 0 && tid == 0) {
                     a.result->iters = k;
@@ -1581,7 +1594,7 @@ __global__ void __launch_bounds__(384, 1) sart_bulk_kernel(SartArgs<T> a, int te
         };
         const bool ok_b = run_pass(a.nzcp, a.row, a.valT, crange.x, crange.y, JB, b_first, b_second, b_body);
         (void)ok_b;
-        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+        if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     }
 }
 

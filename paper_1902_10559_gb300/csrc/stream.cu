@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(512, 1) sart_compact_kernel(StArgs<T, kImplici
 
     const double ppz = st_prologue<T, kImplicit, kBatch>(a, s_red);  // thread 0: empty rows' ||p||^2
     unsigned nbar = 0;
-    if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+    if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     if (!kBatch && wib == 0) {
         const double t = grid_total(a.partials, gridDim.x, lane, 1);
         if (lane == 0) s_tpp = t;
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(512, 1) sart_compact_kernel(StArgs<T, kImplici
             scm = nscm;
         }
         if constexpr (!kBatch) st_rr_partial(rr.sum(), ppz, a.partials, s_red);
-        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+        if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
 
         const int stop = st_stop_test<T, kImplicit, kBatch>(a, k, s_red, s_tpp, &s_stop, nbar);
         if (stop != 0) return;  // stopped (f written back), or a barrier wait failed
@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(512, 1) sart_compact_kernel(StArgs<T, kImplici
             icm = nicm;
             fm = nfm;
         }
-        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
+        if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return;
     }
 }
 

@@ -243,7 +243,7 @@ __device__ __forceinline__ int st_stop_test(const StArgs<T, kImplicit>& a, int k
                 __syncthreads();
             }
         }
-        if (!grid_sync(a.ctl, a.expected * ++nbar, a.timeout_ns, (int)nbar)) return -1;
+        if (!grid_sync(a.ctl, (unsigned long long)a.expected * ++nbar, a.timeout_ns, (int)nbar)) return -1;
         if (ld_volatile(a.ndone) >= a.ns) {
             if (blockIdx.x == 0 && tid == 0) {
                 a.result->iters = k;
